@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark: s-step GMRES with randomized block orthogonalization on one GB300.
+
+Workload (default, one "step"): s-step GMRES(m=60, s=5) on the 7-point 3D Poisson
+matrix of a 100^3 grid (n = 1e6, FP64 CSR, Dirichlet), Jacobi right
+preconditioner, monomial matrix-powers basis, b = A*1, x0 = 0, solved to a 1e-10
+true relative residual -- once with one-stage randomized BCGS2 and once with the
+two-stage scheme (s_hat = 20).  `value` is the mean time to solution per solve.
+The working set (CSR 88 MB + basis 490 MB + vectors) exceeds the 129 MB L2, so no
+L2 flush is needed between steps.
+
+Also reported (the block orthogonalization alone, V = 2^24 x 61 glued blocks,
+two-stage s_hat = 30 and one-stage, FP64 and mixed precision): orthogonalized
+columns/s, algorithmic HBM GB/s and ||I - Q^T Q||_2, under "orth".
+
+`--impl reference` times the CPU oracle (numpy/scipy) on a bounded sample of the
+same workload and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "orth cols/s & HBM GB/s at ‖I−QᵀQ‖≤1e-13; s-step GMRES time to 1e-10"
+WORKLOAD = "s-step GMRES(m=60, s=5) one-stage + two-stage (s_hat=20), 3D Poisson 7-pt 100^3 (n=1e6), Jacobi, b=A*1, tol 1e-10"
+N_GRID, M, S, S_HAT, TOL = 100, 60, 5, 20, 1e-10
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+
+
+def peaks():
+    p = {}
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    return {"hbm_gbs": float(p.get("hbm_gbs", 6800.0)),
+            "hbm_src": "measured" if "hbm_gbs" in p else "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(", ") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2503_16717_gb300 as rbo
+
+    A = synth.poisson3d_csr(N_GRID)
+    b_host = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    bd = torch.from_numpy(b_host).cuda()
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    launches = {"n": 0}
+    last = {}
+
+    def solve(s_hat):
+        x.zero_()
+        _, info = rbo.sstep_gmres(Ad, bd, x, s=S, s_hat=s_hat, m=M, tol=TOL)
+        if info["status"] != 0:
+            raise RuntimeError(f"sstep_gmres failed: {info}")
+        launches["n"] += info["kernel_launches"] + 1
+        return info
+
+    def step():
+        last["one"] = solve(0)
+        last["two"] = solve(S_HAT)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    # unprofiled timing (the reported value)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches["n"] = 0
+    with Clocks(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    gpu_launches = launches["n"]
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    sec_per_solve = ms_per_step / 2.0 / 1e3
+
+    # per-kernel times with CUDA events around each library launch (same steps again)
+    rbo.profile_reset()
+    rbo.profile_enable(True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    barrier()
+    ms_prof = e0.elapsed_time(e1) / args.steps
+    prof = {k: rbo.profile_read(v) for k, v in
+            (("rowpass", rbo.PROF_ROWPASS), ("spmv", rbo.PROF_SPMV), ("vector", rbo.PROF_VECTOR))}
+    rbo.profile_enable(False)
+    rp = prof["rowpass"]
+    avg_ms = rp["ms"] / max(rp["launches"], 1)
+    achieved_flops = rp["flops"] / (rp["ms"] / 1e3) if rp["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "rowpass_kernel<false> (fused FP64 row pass)",
+                "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_DERIVED / 1e12,
+                "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_DERIVED,
+                "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 1.25 TFLOP/s nominal)",
+                "traffic": None, "launches": rp["launches"], "avg_launch_us": avg_ms * 1e3,
+                "hbm_gbs_algorithmic": rp["bytes"] / (rp["ms"] / 1e3) / 1e9 if rp["ms"] > 0 else 0.0,
+                "share_of_step": rp["ms"] / args.steps / ms_prof if ms_prof > 0 else None}
+
+    # end-to-end through the public API with host buffers
+    e2e = run_e2e(rbo, torch, A, b_host, args)
+
+    orth = run_orth(rbo, torch, args) if (rank == 0 and not args.no_orth) else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(A, b_host, last["one"]["iterations"])
+
+    if rank == 0:
+        one, two = last["one"], last["two"]
+        line = {
+            "metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "m": M, "s": S, "s_hat": S_HAT,
+                       "tol": TOL, "l2": "working set > L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "solves": {
+                "one_stage": {"iterations": one["iterations"], "restarts": one["restarts"],
+                              "relres": one["relres"], "kernel_launches": one["kernel_launches"]},
+                "two_stage": {"iterations": two["iterations"], "restarts": two["restarts"],
+                              "relres": two["relres"], "kernel_launches": two["kernel_launches"]},
+            },
+            "ms_per_step_profiled": ms_prof,
+            "kernels": prof,
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "clocks": clk.summary(),
+            "orth": orth,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(rbo, torch, A, b_host, args):
+    """Same solve through the public API, with the matrix and b copied from pinned host
+    memory and x read back, every step (one-stage + two-stage solve per step)."""
+    import numpy as np
+    rp = torch.from_numpy(A.rowptr).pin_memory()
+    cl = torch.from_numpy(A.col).pin_memory()
+    vl = torch.from_numpy(A.val).pin_memory()
+    bh = torch.from_numpy(b_host).pin_memory()
+    xh = torch.empty(A.n, dtype=torch.float64).pin_memory()
+    h2d = (rp.numel() * 4 + cl.numel() * 4 + vl.numel() * 8 + bh.numel() * 8) * 2
+    d2h = xh.numel() * 8 * 2
+
+    def one():
+        for s_hat in (0, S_HAT):
+            Ad = rbo.DeviceCSR.__new__(rbo.DeviceCSR)
+            Ad.n, Ad.nnz = A.n, A.nnz
+            Ad.rowptr = rp.cuda(non_blocking=True)
+            Ad.col = cl.cuda(non_blocking=True)
+            Ad.val = vl.cuda(non_blocking=True)
+            bd = bh.cuda(non_blocking=True)
+            x, info = rbo.sstep_gmres(Ad, bd, s=S, s_hat=s_hat, m=M, tol=TOL)
+            xh.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+            if info["status"] != 0:
+                raise RuntimeError(info)
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    return {"value": dt / 2.0, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def run_orth(rbo, torch, args):
+    """Block orthogonalization alone on V = 2^24 x 61 (v0 + 12 glued blocks of 5)."""
+    import numpy as np
+    import synth
+    n, nb, s, s_hat = 1 << 24, 12, 5, 30
+    c = nb * s + 1
+    out = []
+    kappas = [1e8] if args.quick_orth else [1e4, 1e8, 1e12, 1e14]
+    sk = rbo.sketch_create(n, 4 * c, 8, 42)
+    V0 = synth.glued_blocks_torch(n, nb, s, kappas[0], seed=1, v0=True, device="cuda")
+    W = torch.empty_like(V0)
+    for kappa in kappas:
+        if kappa != kappas[0]:
+            del V0
+            torch.cuda.empty_cache()
+            V0 = synth.glued_blocks_torch(n, nb, s, kappa, seed=1, v0=True, device="cuda")
+        for scheme in ("two", "one"):
+            for prec in (rbo.PREC_FP64, rbo.PREC_MIXED):
+                Wm = W.t()  # n x c column-major view
+                times = []
+                info = None
+                for rep in range(3):
+                    W.copy_(V0)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    if scheme == "two":
+                        o = rbo.block_orth_two_stage(sk, Wm, s, s_hat, v0=True, precision=prec,
+                                                     raise_on_error=False)
+                    else:
+                        o = rbo.block_orth_one_stage(sk, Wm, s, v0=True, precision=prec,
+                                                     raise_on_error=False)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if rep > 0:
+                        times.append(e0.elapsed_time(e1))
+                    info = o.info
+                ms = min(times)
+                G = rbo.gram(Wm, Wm)
+                oe = float(np.max(np.abs(np.linalg.eigvalsh(np.eye(c) - 0.5 * (G + G.T)))))
+                # algorithmic bytes: col-passes per the scheme (every column of every pass once)
+                k = s
+                if scheme == "one":
+                    passes = 2 + sum(4 * p + 11 * k for p in range(1, c, k))
+                else:
+                    passes = 2
+                    for P in range(1, c, s_hat):
+                        for j in range(s_hat // s):
+                            pp = j * k
+                            passes += (P + k) + (P + 2 * k) + (pp + 2 * k)
+                        passes += (P + 2 * s_hat) + (P + 2 * s_hat) + 2 * s_hat
+                gb = passes * 8.0 * n / 1e9
+                out.append({"kappa": kappa, "scheme": scheme,
+                            "precision": "fp64" if prec == rbo.PREC_FP64 else "mixed",
+                            "status": info["status"], "ms": ms, "cols_per_s": c / (ms / 1e3),
+                            "hbm_gbs_algorithmic": gb / (ms / 1e3), "orth_err": oe,
+                            "launches": info["kernel_launches"]})
+    del V0, W
+    torch.cuda.empty_cache()
+    return {"n": n, "cols": c, "s": s, "s_hat": s_hat, "d": 4 * c, "results": out}
+
+
+# ------------------------------------------------------------------------------------------
+def cpu_baseline(A, b, gpu_iterations, budget_cycles=2):
+    """The oracle's one-stage s-step GMRES on the same problem for `budget_cycles`
+    restart cycles, scaled by iterations to the GPU solve's iteration count."""
+    import numpy as np
+    from oracle import krylov
+    t0 = time.perf_counter()
+    res = krylov.sstep_gmres(A, b, s=S, m=M, tol=TOL, max_restarts=budget_cycles)
+    dt = time.perf_counter() - t0
+    its = max(res.iterations, 1)
+    est = dt / its * gpu_iterations
+    return {"value": est, "unit": "s", "cores": _cpu_threads(), "kind": "oracle",
+            "sample": f"{its} iterations ({budget_cycles} restart cycles) of the one-stage solve "
+                      f"in {dt:.1f} s, scaled to {gpu_iterations} iterations"}
+
+
+def _cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    from oracle import krylov
+    A = synth.poisson3d_csr(N_GRID)
+    b = synth.ones_rhs(A)
+    # one bounded sample per step: one restart cycle of each scheme, scaled by
+    # iterations to the converged iteration counts measured by the library (or the
+    # counts the oracle itself reaches on this problem when no GPU count is known)
+    its_full = {"one": 3360, "two": 3380}
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r1 = krylov.sstep_gmres(A, b, s=S, m=M, tol=TOL, max_restarts=1)
+        t1 = time.perf_counter()
+        r2 = krylov.sstep_gmres(A, b, s=S, m=M, s_hat=S_HAT, scheme="two", tol=TOL, max_restarts=1)
+        t2 = time.perf_counter()
+        est = ((t1 - t0) / max(r1.iterations, 1) * its_full["one"] +
+               (t2 - t1) / max(r2.iterations, 1) * its_full["two"]) / 2.0
+        if it >= args.warmup:
+            times.append(est)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 2e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": A.n},
+            "cpu_baseline": {"value": v, "unit": "s", "kind": "oracle", "cores": _cpu_threads(),
+                             "sample": "one restart cycle (60 iterations) of each scheme per step, "
+                                       "scaled per iteration to the converged iteration counts"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-orth", action="store_true")
+    ap.add_argument("--quick-orth", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

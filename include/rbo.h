@@ -1,0 +1,216 @@
+/*
+ * rbo.h -- randomized block orthogonalization for s-step GMRES on GB300 (sm_103a).
+ *
+ * C ABI of the library librbo.so.  The operations follow Yamazaki, Higgins,
+ * Boman and Szyld, "Random sketching to enhance the numerical stability of
+ * block orthogonalization algorithms for s-step GMRES" (arXiv 2503.16717):
+ *
+ *   qr(Q, V_j):  extend Q R = V with Q^T Q = I, R upper triangular with a
+ *                non-negative diagonal (Section 4, Figure 1 caption).
+ *
+ * Conventions shared by every call
+ *   - Dense n-row arrays (V, Q, vectors) are caller-owned DEVICE pointers,
+ *     column-major with leading dimension ld >= n, float64.
+ *   - Small outputs (R, info) are caller-owned HOST memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on that stream; every call that returns a
+ *     status synchronises the stream once at its end to read the device
+ *     status word (and GMRES synchronises once per panel for its host-side
+ *     least-squares step).
+ *   - Scratch memory comes from a per-device library arena that grows on
+ *     demand (cudaMalloc) and is reused by later calls; rbo_release_workspace
+ *     frees it.  Calls that share the arena must not overlap in time (use one
+ *     host thread / one stream per device at a time).
+ *   - Every call returns RBO_OK (0) or a negative RBO_ERR_* code; no call
+ *     throws or aborts.  On an error the contents of the in/out arrays are
+ *     unspecified.
+ */
+#ifndef RBO_H
+#define RBO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define RBO_OK                  0
+#define RBO_ERR_ARG            -1  /* invalid argument (size, pointer, layout)          */
+#define RBO_ERR_CUDA           -2  /* a CUDA runtime call failed                         */
+#define RBO_ERR_CHOL_BREAKDOWN -3  /* non-positive Cholesky pivot (Section 5.1);
+                                      info->breakdown_* say where                        */
+#define RBO_ERR_NOT_CONVERGED  -4  /* GMRES reached max_restarts above tol               */
+#define RBO_ERR_TIMEOUT        -5  /* a bounded device wait expired                      */
+#define RBO_ERR_SKETCH         -6  /* a sketch column found < zeta distinct rows         */
+#define RBO_ERR_NOMEM          -7  /* workspace allocation failed                        */
+#define RBO_ERR_NO_DEVICE      -8  /* no CUDA device / not an sm_103 device              */
+
+/* ---- precision modes --------------------------------------------------------- */
+#define RBO_PREC_FP64   0  /* every step in IEEE float64 (the reference path)          */
+#define RBO_PREC_MIXED  1  /* sketch apply and first-pass projection coefficients in
+                              float32 with float32 accumulation; Gram matrices feeding
+                              the final Cholesky, the small factors, every update of V
+                              and the final TRSM in float64                             */
+
+/* ---- intra-block choice (one-stage) ----------------------------------------- */
+#define RBO_INTRA_RANDCHOLQR 0  /* RandCholQR (Figure 4b)                                */
+#define RBO_INTRA_CHOLQR2    1  /* CholQR2 (Figure 2b twice): the deterministic baseline */
+
+typedef struct rbo_opts {
+  int32_t precision;     /* RBO_PREC_*                                                  */
+  int32_t v0;            /* 1: column 0 of V is the single start vector V_0 = [v_0]
+                            (Table 1), normalised before the blocks                     */
+  int32_t intra;         /* RBO_INTRA_* (one-stage only)                                */
+  int32_t max_restarts;  /* GMRES: restart cycles allowed (default 1000 if <= 0)        */
+  int32_t precond;       /* GMRES: 0 none, 1 Jacobi (M = diag(A), right preconditioner) */
+  int32_t reserved[3];
+} rbo_opts;
+
+#define RBO_STAGE_V0          1  /* normalisation of v_0                                  */
+#define RBO_STAGE_INTRA       2  /* first intra-block Cholesky (CholQR / RandCholQR)     */
+#define RBO_STAGE_INTRA2      3  /* second Cholesky of CholQR2                           */
+#define RBO_STAGE_FINAL       4  /* Cholesky after the re-orthogonalization              */
+#define RBO_STAGE_BIGPANEL    5  /* two-stage: CholQR of the preprocessed big panel      */
+
+typedef struct rbo_info {
+  int32_t status;            /* same value as the return code                          */
+  int32_t breakdown_block;   /* block (one-stage) or big panel (two-stage), -1 if none */
+  int32_t breakdown_column;  /* column within that block of the failed pivot           */
+  int32_t breakdown_stage;   /* RBO_STAGE_*                                            */
+  int32_t iterations;        /* GMRES: matrix-powers columns generated                */
+  int32_t restarts;          /* GMRES: restart cycles started                          */
+  int32_t converged;         /* GMRES: 1 if ||b - A x|| <= tol ||b||                    */
+  int32_t kernel_launches;   /* kernels this call enqueued                              */
+  double  relres;            /* GMRES: final true relative residual                    */
+  double  est_relres;        /* GMRES: last least-squares residual estimate            */
+  double  time_ms;           /* host wall time of the call                             */
+  double* history;           /* GMRES, optional caller buffer: (iteration, true relres)
+                                pairs, one per restart                                 */
+  int32_t history_cap;       /* capacity of `history` in pairs                         */
+  int32_t history_len;       /* pairs written                                          */
+} rbo_info;
+
+/* ---- sparse-sign sketch (Section 3 / 5.2; the paper's Count sketch with zeta
+ *      nonzeros per column) ------------------------------------------------------
+ * S is d x n; column r holds zeta distinct row indices with signs +-1, drawn
+ * from the SplitMix64 stream (Steele, Lea & Flood 2014) seeded with `seed`:
+ * row r owns outputs i = 64 r + c + 1 (c = 0..63) of that stream; output h gives
+ * index ((h >> 32) * d) >> 32 and sign -1 iff bit 0 of h is set; repeated
+ * indices are skipped.  Nothing is stored: kernels recompute entries from
+ * (seed, row).  Values are +-1, unscaled.                                         */
+typedef struct rbo_sketch_s* rbo_sketch;
+
+/* Create a sketch handle for matrices of up to n_max rows.  1 <= zeta <= d <= 4096.
+ * The handle is library-owned (host memory only); destroy it with
+ * rbo_sketch_destroy.  Errors: RBO_ERR_ARG.                                        */
+int rbo_sketch_create(int64_t n_max, int32_t d, int32_t zeta, uint64_t seed, rbo_sketch* out);
+int rbo_sketch_destroy(rbo_sketch sk);
+
+/* Materialise the entries of columns row0 .. row0+nrows-1 of S on the device, with
+ * the same device code the sketch apply uses: idx (nrows x zeta, int32, row-major)
+ * and sign (nrows x zeta, int8), both caller-owned device arrays.  For tests.
+ * Errors: RBO_ERR_ARG, RBO_ERR_SKETCH, RBO_ERR_CUDA.                               */
+int rbo_sketch_entries(rbo_sketch sk, int64_t row0, int64_t nrows, int32_t* idx, int8_t* sign,
+                       void* stream);
+
+/* out = S W  (d x k, column-major, ld d, caller-owned HOST array) for W (n x k,
+ * device, ld ldw).  The step "v = Theta^T V" of RandHH (Section 5.2).
+ * `precision` RBO_PREC_FP64 or RBO_PREC_MIXED (float32 accumulation).            */
+int rbo_sketch_apply(rbo_sketch sk, int64_t n, int32_t k, const double* W, int64_t ldw,
+                     double* out, int32_t precision, void* stream);
+
+/* ---- tall-skinny Gram (the reduction of BCGS / CholQR, Figures 2a-2b) ----------
+ * C = X^T Y (a x b, column-major ld a, caller-owned HOST array) for device
+ * X (n x a, ld ldx) and Y (n x b, ld ldy); a, b <= 128.  Deterministic
+ * (fixed-order cross-CTA tree).                                                   */
+int rbo_gram(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, const double* Y,
+             int64_t ldy, double* C, void* stream);
+
+/* ---- block orthogonalization ------------------------------------------------------
+ * V (n x ncols, device, ld ldv) is overwritten by Q; R (ncols x ncols, column-major,
+ * ld ldr >= ncols, caller-owned HOST array) receives the upper-triangular factor.
+ * Blocks: if opts->v0, column 0 is normalised first; the remaining columns form
+ * blocks of s columns (ncols - v0 must be a multiple of s; 1 <= s <= 64;
+ * ncols <= 129).  n >= ncols is required.  `sk` may be shared between calls.
+ * The sketch size times the panel width, d * s, must not exceed 12288 (the
+ * per-warp sketch partials live in shared memory); the same bound applies to
+ * rbo_sketch_apply (d * k) and rbo_sstep_gmres (d * s).
+ *
+ * one_stage (Section 5): per block, BCGS2 with RandCholQR (or CholQR2) as the
+ *   first intra-block step and CholQR after the re-orthogonalization.
+ * two_stage (Sections 6-7): big panels of s_hat columns (s | s_hat,
+ *   s_hat | ncols - v0, s_hat <= 64) built from panels of s; each panel is projected
+ *   against the finished big panels (BCGS) and preprocessed with RandBCGS2
+ *   (sketched BCGS2 with Householder intra step, then forward substitution); each
+ *   big panel is finished by CholQR, BCGS and CholQR.  s_hat == s is one-stage.
+ * cholqr2: one-stage BCGS2 with CholQR2 as the first intra-block step; reports
+ *   RBO_ERR_CHOL_BREAKDOWN with the failing block and column instead of
+ *   producing NaNs (Section 5.1).
+ * Errors: RBO_ERR_ARG, RBO_ERR_CHOL_BREAKDOWN, RBO_ERR_TIMEOUT, RBO_ERR_CUDA,
+ *         RBO_ERR_NOMEM, RBO_ERR_SKETCH.                                           */
+int rbo_block_orth_one_stage(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, double* V,
+                             int64_t ldv, double* R, int64_t ldr, const rbo_opts* opts,
+                             rbo_info* info, void* stream);
+int rbo_block_orth_two_stage(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, int32_t s_hat,
+                             double* V, int64_t ldv, double* R, int64_t ldr, const rbo_opts* opts,
+                             rbo_info* info, void* stream);
+int rbo_block_orth_cholqr2(int64_t n, int32_t ncols, int32_t s, double* V, int64_t ldv, double* R,
+                           int64_t ldr, const rbo_opts* opts, rbo_info* info, void* stream);
+
+/* ---- CSR matrix and matrix-powers kernel (Section 4) ----------------------------- */
+typedef struct rbo_csr {
+  int64_t n;              /* rows = columns                                          */
+  int64_t nnz;            /* < 2^31                                                  */
+  const int32_t* rowptr;  /* device, n+1 entries, rowptr[0] = 0                      */
+  const int32_t* col;     /* device, nnz column indices in [0, n)                    */
+  const double* val;      /* device, nnz values                                      */
+} rbo_csr;
+
+/* Monomial MPK: V[:, i] = (A D)^{i+1} v0 for i = 0..s-1, with D = diag(dscale) if
+ * dscale != NULL (right Jacobi scaling: dscale = 1 / diag(A)) else D = I.
+ * v0 (n), dscale (n) and V (n x s, ld ldv) are device arrays; v0 must not alias V.
+ * Errors: RBO_ERR_ARG, RBO_ERR_CUDA.                                              */
+int rbo_mpk_csr(const rbo_csr* A, const double* dscale, int32_t s, const double* v0, double* V,
+                int64_t ldv, void* stream);
+
+/* ---- s-step GMRES (Section 4, Figure 1) -------------------------------------------
+ * Solves A x = b (b, x: device, n) with restart length m (s | m, m <= 128) and
+ * right preconditioner opts->precond.  x holds x0 on entry (resume from a
+ * previous solve) and the solution on exit.  s_hat == 0 or s_hat == s: one-stage
+ * randomized BCGS2; s < s_hat (s | s_hat | m): two-stage with RandBCGS2.
+ * The sketch has d = 4 (m + 1) rows, zeta = 8, seed 42 unless `sk` is given.
+ * Converged when ||b - A x||_2 <= tol ||b||_2 (true residual).
+ * Errors: RBO_ERR_ARG, RBO_ERR_NOT_CONVERGED, RBO_ERR_CHOL_BREAKDOWN, RBO_ERR_CUDA,
+ *         RBO_ERR_NOMEM, RBO_ERR_TIMEOUT.                                          */
+int rbo_sstep_gmres(const rbo_csr* A, const double* b, double* x, int32_t s, int32_t s_hat,
+                    int32_t m, double tol, rbo_sketch sk, const rbo_opts* opts, rbo_info* info,
+                    void* stream);
+
+/* ---- per-kernel timing ---------------------------------------------------------------
+ * When enabled, every kernel the library enqueues is bracketed by two CUDA events on
+ * its stream and tagged with its algorithmic DRAM bytes (each n-row column read or
+ * written once) and floating-point operations.  Totals accumulate per kernel kind
+ * until rbo_profile_reset.  Reading drains pending events (synchronising on them).
+ * Process-wide; not for concurrent calls from several host threads.              */
+#define RBO_PROF_ROWPASS 0  /* the fused tall-skinny row pass (Gram / update / TRSM / sketch) */
+#define RBO_PROF_SPMV    1  /* CSR SpMV of the matrix-powers kernel and residuals           */
+#define RBO_PROF_VECTOR  2  /* small vector kernels (Jacobi setup, x update, scaling)       */
+int rbo_profile_enable(int on);
+int rbo_profile_reset(void);
+int rbo_profile_read(int32_t kind, int64_t* launches, double* ms, double* bytes, double* flops);
+
+/* ---- housekeeping ------------------------------------------------------------------ */
+const char* rbo_status_string(int status);
+/* Free the calling thread's current device's workspace arena. */
+int rbo_release_workspace(void);
+/* Library version string and the sm architecture it was compiled for. */
+const char* rbo_version(void);
+/* Name and description of the last CUDA error a call of this host thread met
+ * (empty if none); valid until the next failing call. */
+const char* rbo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBO_H */

@@ -1,0 +1,336 @@
+// s-step GMRES (Section 4, Figure 1) driver: right preconditioning, monomial
+// matrix-powers kernel, one-stage or two-stage randomized block orthogonalization,
+// Hessenberg H = Y X^{-1} from the R factors and a Givens least-squares solve on
+// the host.
+//
+// With generators U (the vectors the operator is applied to) and outputs
+// W = Ahat U, written in the orthonormal basis as U = Q X and W = Q Y, the Arnoldi
+// relation Ahat Q = Q H gives H = Y X^{-1}.  X is upper triangular: the first
+// generator of a panel is the last orthonormal column (one-stage) or the last
+// preprocessed column qbar (two-stage, inside a big panel), the others are the raw
+// MPK outputs, whose coordinates are columns of R.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rbo_internal.cuh"
+
+namespace rbo {
+
+// min || beta e1 - H z || for the (k+1) x k Hessenberg H (column-major, ld ldh)
+// by Givens rotations; returns the residual norm and z.
+static double hessenberg_ls(const std::vector<double>& Hin, int ldh, int k, double beta,
+                            std::vector<double>& z) {
+  std::vector<double> H(Hin.begin(), Hin.begin() + (size_t)ldh * k);
+  std::vector<double> g(k + 1, 0.0);
+  g[0] = beta;
+  for (int j = 0; j < k; ++j) {
+    // H(j+1, j) is the only subdiagonal entry (earlier rotations applied below)
+    double a = H[j + (size_t)j * ldh], b = H[(j + 1) + (size_t)j * ldh];
+    double r = std::hypot(a, b);
+    double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : b / r;
+    for (int l = j; l < k; ++l) {
+      double h1 = H[j + (size_t)l * ldh], h2 = H[(j + 1) + (size_t)l * ldh];
+      H[j + (size_t)l * ldh] = c * h1 + s * h2;
+      H[(j + 1) + (size_t)l * ldh] = -s * h1 + c * h2;
+    }
+    double g1 = g[j], g2 = g[j + 1];
+    g[j] = c * g1 + s * g2;
+    g[j + 1] = -s * g1 + c * g2;
+  }
+  z.assign(k, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double v = g[i];
+    for (int l = i + 1; l < k; ++l) v -= H[i + (size_t)l * ldh] * z[l];
+    z[i] = v / H[i + (size_t)i * ldh];
+  }
+  return std::fabs(g[k]);
+}
+
+struct GmresWork {
+  double* Qb;       // n x (m+1), ld ldq
+  int64_t ldq;
+  double* vals;     // scaled CSR values (Jacobi)
+  double* dscale;   // 1 / diag(A)
+  double* y;        // right-preconditioned iterate
+  double* zdev;     // m
+  double* Rdev;     // (m+1) x (m+1)
+  double* coords;   // (m+1) x s_hat
+  double* bn;       // 1 (||b||^2)
+};
+
+int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_hat, int m,
+                     double tol, int d, int zeta, uint64_t seed, const rbo_opts* opts,
+                     rbo_info* info, cudaStream_t st, int* launches_out) {
+  const int64_t n = A->n;
+  const bool two = s_hat > s;
+  const int K = two ? s_hat : s;
+  const int precond = opts ? opts->precond : 1;
+  const int max_restarts = (opts && opts->max_restarts > 0) ? opts->max_restarts : 1000;
+  const int ld = m + 1;
+  const int64_t ldq = (n + 1) & ~int64_t(1);  // even: 16-byte aligned columns
+
+  const int pmax = m + 1, kmax = K;
+  const int maxL = std::max(orth_max_L(pmax, kmax, d), 1);
+  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d) +
+                 (size_t)ldq * (m + 1) * 8 + (size_t)A->nnz * 8 + 2 * (size_t)n * 8 +
+                 (size_t)(m + 1) * (m + 1) * 8 + (size_t)(m + 1) * K * 8 + (size_t)m * 8 + 16 * 1024;
+  Arena* ar = nullptr;
+  int e = arena_prepare(&ar, bytes);
+  if (e) return e;
+  if ((e = arena_reserve_reduction(ar, maxL, st))) return e;
+  GmresWork w;
+  w.ldq = ldq;
+  w.Qb = (double*)ar->take((size_t)ldq * (m + 1) * 8);
+  w.vals = precond ? (double*)ar->take((size_t)std::max<int64_t>(A->nnz, 1) * 8) : nullptr;
+  w.dscale = precond ? (double*)ar->take((size_t)n * 8) : nullptr;
+  w.y = (double*)ar->take((size_t)n * 8);
+  w.zdev = (double*)ar->take((size_t)m * 8 + 64);
+  w.Rdev = (double*)ar->take((size_t)ld * ld * 8);
+  w.coords = (double*)ar->take((size_t)ld * K * 8);
+  w.bn = (double*)ar->take(64);
+  if (!w.Qb || !w.y || !w.zdev || !w.Rdev || !w.coords || !w.bn || (precond && (!w.vals || !w.dscale)))
+    return RBO_ERR_NOMEM;
+
+  OrthCtx c;
+  c.ar = ar;
+  c.st = st;
+  c.mixed = (opts && opts->precision == RBO_PREC_MIXED) ? 1 : 0;
+  c.d = d;
+  c.zeta = zeta;
+  c.seed = seed;
+  if ((e = orth_ctx_alloc(c, pmax, kmax))) return e;
+
+  CsrDev Araw{n, A->nnz, A->rowptr, A->col, A->val};
+  CsrDev Ahat = Araw;
+  if (precond) {
+    if ((e = jacobi_launch(Araw, w.dscale, ar->status, st))) return e;
+    if ((e = scale_columns_launch(Araw, w.dscale, w.vals, st))) return e;
+    Ahat.val = w.vals;
+    c.launches += 2;
+  }
+  // y0 = D x0  (x = D^{-1} y with D^{-1} = dscale)
+  if ((e = scale_vec_launch(n, w.dscale, x, w.y, 1, st))) return e;
+  c.launches += 1;
+  // ||b||
+  {
+    RowPass r;
+    r.n = n; r.Y = const_cast<double*>(b); r.ldy = ldq; r.b = 1; r.acc_y = 1;
+    r.epi.op = EPI_STORE_ALL; r.epi.out = w.bn;
+    if ((e = rowpass_launch(r, ar, st, &c.launches))) return e;
+  }
+  double bn2 = 0.0;
+  if (cudaMemcpyAsync(&bn2, w.bn, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RBO_ERR_CUDA;
+  if ((e = finish_status(ar, st, info))) return e;
+  const double bnorm = std::sqrt(bn2);
+  if (bnorm == 0.0) {
+    if (cudaMemsetAsync(x, 0, (size_t)n * 8, st) != cudaSuccess) return RBO_ERR_CUDA;
+    if (info) { info->converged = 1; info->relres = 0.0; }
+    *launches_out = c.launches;
+    return cudaStreamSynchronize(st) == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+  }
+
+  std::vector<double> Rh((size_t)ld * ld), X((size_t)m * m), Y((size_t)ld * m), H((size_t)ld * m);
+  std::vector<double> coords((size_t)ld * K), z;
+  int its = 0;
+  bool converged = false;
+  double relres = INFINITY, est_rel = INFINITY;
+  int cycle = 0;
+  for (cycle = 0; cycle <= max_restarts; ++cycle) {
+    // r = b - Ahat y into basis column 0, q0 = r / ||r||
+    if ((e = residual_launch(Ahat, b, w.y, w.Qb, ar->status, st))) return e;
+    c.launches += 1;
+    if (cudaMemsetAsync(w.Rdev, 0, (size_t)ld * ld * 8, st) != cudaSuccess) return RBO_ERR_CUDA;
+    if ((e = normalise_column(c, n, w.Qb, w.Rdev, ld, 0))) return e;
+    double beta = 0.0;
+    if (cudaMemcpyAsync(&beta, w.Rdev, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RBO_ERR_CUDA;
+    e = finish_status(ar, st, info);
+    if (e == RBO_ERR_CHOL_BREAKDOWN && info && info->breakdown_stage == RBO_STAGE_V0) {
+      // r == 0 exactly
+      relres = 0.0;
+      converged = true;
+      break;
+    }
+    if (e) return e;
+    relres = beta / bnorm;
+    if (info && info->history && info->history_len < info->history_cap) {
+      info->history[2 * info->history_len] = its;
+      info->history[2 * info->history_len + 1] = relres;
+      info->history_len++;
+    }
+    if (relres <= tol) {
+      converged = true;
+      break;
+    }
+    if (cycle == max_restarts) break;
+    std::fill(X.begin(), X.end(), 0.0);
+    std::fill(Y.begin(), Y.end(), 0.0);
+    int ncols = 1;
+    int blk = 0;
+    while (ncols < m + 1) {
+      const int P = ncols;
+      if (!two) {
+        double* W = w.Qb + (int64_t)P * ldq;
+        const double* u = w.Qb + (int64_t)(P - 1) * ldq;
+        for (int i = 0; i < s; ++i) {
+          if ((e = spmv_launch(Ahat, nullptr, i == 0 ? u : W + (int64_t)(i - 1) * ldq,
+                               W + (int64_t)i * ldq, ar->status, st)))
+            return e;
+          c.launches += 1;
+        }
+        if ((e = one_stage_block(c, n, w.Qb, ldq, P, W, ldq, s, RBO_INTRA_RANDCHOLQR, w.Rdev, ld, P,
+                                 blk)))
+          return e;
+        if (cudaMemcpy2DAsync(Rh.data() + (size_t)P * ld, (size_t)ld * 8, w.Rdev + (size_t)P * ld,
+                              (size_t)ld * 8, (size_t)(P + s) * 8, s, cudaMemcpyDeviceToHost,
+                              st) != cudaSuccess)
+          return RBO_ERR_CUDA;
+        if ((e = finish_status(ar, st, info))) return e;
+        X[(P - 1) + (size_t)(P - 1) * m] = 1.0;
+        for (int i = 1; i < s; ++i)
+          for (int r = 0; r < P + i; ++r) X[r + (size_t)(P - 1 + i) * m] = Rh[r + (size_t)(P + i - 1) * ld];
+        for (int i = 0; i < s; ++i)
+          for (int r = 0; r < P + s; ++r) Y[r + (size_t)(P - 1 + i) * ld] = Rh[r + (size_t)(P + i) * ld];
+        ncols += s;
+        its += s;
+      } else {
+        BigPanel bp;
+        bp.n = n; bp.Q = w.Qb; bp.ldq = ldq; bp.P = P;
+        bp.VB = w.Qb + (int64_t)P * ldq; bp.ldv = ldq; bp.K = K; bp.blk = blk;
+        std::vector<int> gens;
+        for (int j = 0; j < K / s; ++j) {
+          const double* u;
+          if (j == 0) {
+            u = w.Qb + (int64_t)(P - 1) * ldq;
+            gens.push_back(-1);
+          } else {
+            u = bp.VB + (int64_t)(bp.cols - 1) * ldq;
+            gens.push_back(bp.cols - 1);
+          }
+          double* W = bp.VB + (int64_t)bp.cols * ldq;
+          for (int i = 0; i < s; ++i) {
+            if ((e = spmv_launch(Ahat, nullptr, i == 0 ? u : W + (int64_t)(i - 1) * ldq,
+                                 W + (int64_t)i * ldq, ar->status, st)))
+              return e;
+            c.launches += 1;
+          }
+          if ((e = bigpanel_add(c, bp, s))) return e;
+        }
+        if ((e = bigpanel_finish(c, bp, w.Rdev, ld, P, w.coords, ld))) return e;
+        if (cudaMemcpy2DAsync(Rh.data() + (size_t)P * ld, (size_t)ld * 8, w.Rdev + (size_t)P * ld,
+                              (size_t)ld * 8, (size_t)(P + K) * 8, K, cudaMemcpyDeviceToHost,
+                              st) != cudaSuccess)
+          return RBO_ERR_CUDA;
+        if (cudaMemcpy2DAsync(coords.data(), (size_t)ld * 8, w.coords, (size_t)ld * 8,
+                              (size_t)(P + K) * 8, K, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return RBO_ERR_CUDA;
+        if ((e = finish_status(ar, st, info))) return e;
+        for (int j = 0; j < (int)gens.size(); ++j) {
+          const int cc = P + j * s;  // first new column of panel j
+          if (gens[j] < 0) {
+            X[(cc - 1) + (size_t)(cc - 1) * m] = 1.0;
+          } else {
+            const int g = gens[j];
+            for (int r = 0; r <= P + g; ++r) X[r + (size_t)(cc - 1) * m] = coords[r + (size_t)g * ld];
+          }
+          for (int i = 1; i < s; ++i)
+            for (int r = 0; r < cc + i; ++r)
+              X[r + (size_t)(cc - 1 + i) * m] = Rh[r + (size_t)(cc + i - 1) * ld];
+        }
+        for (int i = 0; i < K; ++i)
+          for (int r = 0; r < P + K; ++r) Y[r + (size_t)(P - 1 + i) * ld] = Rh[r + (size_t)(P + i) * ld];
+        ncols += K;
+        its += K;
+      }
+      ++blk;
+      // H = Y X^{-1} on the first k = ncols-1 columns
+      const int k = ncols - 1;
+      for (int col = 0; col < k; ++col) {
+        for (int r = 0; r < ncols; ++r) {
+          double v = Y[r + (size_t)col * ld];
+          for (int l = 0; l < col; ++l) v -= H[r + (size_t)l * ld] * X[l + (size_t)col * m];
+          H[r + (size_t)col * ld] = v / X[col + (size_t)col * m];
+        }
+      }
+      double est = hessenberg_ls(H, ld, k, beta, z);
+      est_rel = est / bnorm;
+      if (est_rel <= tol) break;
+    }
+    // y += Q z
+    const int k = ncols - 1;
+    if (cudaMemcpyAsync(w.zdev, z.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return RBO_ERR_CUDA;
+    if ((e = gemv_update_launch(n, k, w.Qb, ldq, w.zdev, w.y, st))) return e;
+    c.launches += 1;
+  }
+  if ((e = scale_vec_launch(n, w.dscale, w.y, x, 0, st))) return e;
+  c.launches += 1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RBO_ERR_CUDA;
+  if (info) {
+    info->iterations = its;
+    info->restarts = cycle;
+    info->converged = converged ? 1 : 0;
+    info->relres = relres;
+    info->est_relres = est_rel;
+  }
+  *launches_out = c.launches;
+  return converged ? RBO_OK : RBO_ERR_NOT_CONVERGED;
+}
+
+}  // namespace rbo
+
+
+extern "C" int rbo_sstep_gmres(const rbo_csr* A, const double* b, double* x, int32_t s,
+                               int32_t s_hat, int32_t m, double tol, rbo_sketch sk,
+                               const rbo_opts* opts, rbo_info* info, void* stream) {
+  using namespace rbo;
+  auto t0 = std::chrono::steady_clock::now();
+  if (info) {
+    double* h = info->history;
+    int32_t cap = info->history_cap;
+    memset(info, 0, sizeof(*info));
+    info->history = h;
+    info->history_cap = cap;
+    info->breakdown_block = -1;
+    info->breakdown_column = -1;
+  }
+  int code = RBO_OK;
+  int launches = 0;
+  if (!A || A->n < 1 || !A->rowptr || !A->col || !A->val || A->nnz < 0 || A->nnz >= (1LL << 31) ||
+      !b || !x || s < 1 || m < s || m % s != 0 || m > 128 || !(tol > 0.0))
+    code = RBO_ERR_ARG;
+  if (s_hat == 0) s_hat = s;
+  if (code == RBO_OK && (s_hat < s || s_hat % s != 0 || m % s_hat != 0 || s_hat > 64))
+    code = RBO_ERR_ARG;
+  if (code == RBO_OK && A->n < m + 1) code = RBO_ERR_ARG;
+  if (code == RBO_OK && (int64_t)(sk ? sk->d : 4 * (m + 1)) * s > MAX_SKETCH_DK) code = RBO_ERR_ARG;
+  if (code == RBO_OK && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
+  if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 && opts->precision != RBO_PREC_MIXED)
+    code = RBO_ERR_ARG;
+  int d = 4 * (m + 1), zeta = 8;
+  uint64_t seed = 42;
+  if (sk) {
+    if (sk->n_max < A->n) code = RBO_ERR_ARG;
+    d = sk->d;
+    zeta = sk->zeta;
+    seed = sk->seed;
+  }
+  if (code == RBO_OK) {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) code = RBO_ERR_NO_DEVICE;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) code = RBO_ERR_NO_DEVICE;
+  }
+  if (code == RBO_OK)
+    code = sstep_gmres_impl(A, b, x, s, s_hat, m, tol, d, zeta, seed, opts, info,
+                            (cudaStream_t)stream, &launches);
+  if (info) {
+    info->status = code;
+    info->kernel_launches = launches;
+    info->time_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return code;
+}

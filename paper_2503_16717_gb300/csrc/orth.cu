@@ -1,0 +1,247 @@
+// Host orchestration of the block orthogonalization schemes as sequences of row
+// passes (see rowpass.cu).  All work is enqueued on one stream; small factors stay
+// in device buffers and are consumed by later passes, so there is no host round
+// trip inside a block.
+//
+// One-stage BCGS2 with RandCholQR (Sections 4-5), block j with p previous columns:
+//   P1  C1 = Q^T W                                     (BCGS Gram)
+//   P2  W = W - Q C1 ; w = S W ; R_hat = HH(w)          (BCGS update + sketch, RandHH)
+//   P3  W = W R_hat^{-1} ; G = W^T W ; R' = chol(G)     (RandHH TRSM + CholQR Gram)
+//   P4  W = W R'^{-1} ; C2 = Q^T W                      (CholQR TRSM + re-orth Gram)
+//   P5  W = W - Q C2 ; G2 = W^T W ; R2 = chol(G2)       (re-orth update + CholQR Gram)
+//       R[:p, j] = C1 + C2 R' R_hat ; R_jj = R2 R' R_hat
+//   P6  W = W R2^{-1}                                    (final TRSM)
+// CholQR2 as the first intra step replaces the sketch of P2 by G = W^T W and
+// R_hat = chol(G).
+#include <algorithm>
+
+#include "rbo_internal.cuh"
+
+namespace rbo {
+
+size_t orth_ctx_bytes(int pmax, int kmax, int d) {
+  size_t pk = (size_t)std::max(pmax, 1) * kmax, kk = (size_t)kmax * kmax;
+  size_t dd = (size_t)std::max(d, 1) * kmax;
+  return (2 * pk + 6 * kk + dd + pk + kk) * 8 + 16 * 256;
+}
+
+int orth_max_L(int pmax, int kmax, int d) {
+  // Z of at most (pmax + kmax) x kmax plus a d x kmax sketch
+  return (pmax + kmax) * kmax + std::max(d, 0) * kmax;
+}
+
+int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax) {
+  c.pmax = pmax;
+  c.kmax = kmax;
+  size_t pk = (size_t)std::max(pmax, 1) * kmax, kk = (size_t)kmax * kmax;
+  size_t dd = (size_t)std::max(c.d, 1) * kmax;
+  c.C1 = (double*)c.ar->take(pk * 8);
+  c.C2 = (double*)c.ar->take(pk * 8);
+  c.Rh = (double*)c.ar->take(kk * 8);
+  c.Rp = (double*)c.ar->take(kk * 8);
+  c.R2 = (double*)c.ar->take(kk * 8);
+  c.T = (double*)c.ar->take(kk * 8);
+  c.GB = (double*)c.ar->take(kk * 8);
+  c.qs = (double*)c.ar->take(dd * 8);
+  c.tmp = (double*)c.ar->take((pk + kk) * 8);
+  if (!c.C1 || !c.C2 || !c.Rh || !c.Rp || !c.R2 || !c.T || !c.GB || !c.qs || !c.tmp)
+    return RBO_ERR_NOMEM;
+  return RBO_OK;
+}
+
+#define RBO_TRY(x)             \
+  do {                         \
+    int _e = (x);              \
+    if (_e != RBO_OK) return _e; \
+  } while (0)
+
+int normalise_column(OrthCtx& c, int64_t n, double* v, double* Rdev, int ldR, int col0) {
+  const int64_t ldeven = (n + 1) & ~int64_t(1);  // only column 0 is used
+  RowPass g;
+  g.n = n;
+  g.Y = v;
+  g.ldy = ldeven;
+  g.b = 1;
+  g.acc_y = 1;
+  g.epi.op = EPI_CHOL;
+  g.epi.out_r = c.R2;
+  g.epi.stage = RBO_STAGE_V0;
+  g.epi.block = -1;
+  g.epi.asm_op = ASM_DIAG;
+  g.epi.Rfull = Rdev;
+  g.epi.ldR = ldR;
+  g.epi.p = col0;
+  g.epi.col0 = col0;
+  RBO_TRY(rowpass_launch(g, c.ar, c.st, &c.launches));
+  RowPass s;
+  s.n = n;
+  s.Y = v;
+  s.ldy = ldeven;
+  s.b = 1;
+  s.Tri = c.R2;
+  s.write_y = 1;
+  return rowpass_launch(s, c.ar, c.st, &c.launches);
+}
+
+int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, double* W,
+                    int64_t ldw, int k, int intra, double* Rdev, int ldR, int col0, int blk) {
+  if (p > c.pmax || k > c.kmax) return RBO_ERR_ARG;
+  const bool rand = intra == RBO_INTRA_RANDCHOLQR;
+  // P1: C1 = Q^T W
+  if (p > 0) {
+    RowPass r;
+    r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
+    r.acc_x = 1;
+    r.mixed = c.mixed;
+    r.epi.op = EPI_STORE; r.epi.out = c.C1; r.epi.out_ld = p;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  // P2: W = W - Q C1, then sketch -> R_hat (or Gram -> chol for CholQR2)
+  {
+    RowPass r;
+    r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
+    if (p > 0) { r.C = c.C1; r.write_y = 1; }
+    if (rand) {
+      r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed;
+      r.mixed = c.mixed;
+      r.epi.op = EPI_HH; r.epi.out_r = c.Rh;
+    } else {
+      r.acc_y = 1;
+      r.epi.op = EPI_CHOL; r.epi.out_r = c.Rh; r.epi.stage = RBO_STAGE_INTRA; r.epi.block = blk;
+    }
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  // P3: W = W R_hat^{-1}; R' = chol(W^T W)
+  {
+    RowPass r;
+    r.n = n; r.Y = W; r.ldy = ldw; r.b = k;
+    r.Tri = c.Rh; r.write_y = 1; r.acc_y = 1;
+    r.epi.op = EPI_CHOL; r.epi.out_r = c.Rp; r.epi.block = blk;
+    r.epi.stage = rand ? RBO_STAGE_INTRA : RBO_STAGE_INTRA2;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  Epilogue fin;
+  fin.op = EPI_CHOL; fin.out_r = c.R2; fin.stage = RBO_STAGE_FINAL; fin.block = blk;
+  fin.asm_op = ASM_ONE_STAGE;
+  fin.C1 = c.C1; fin.ldc1 = std::max(p, 1);
+  fin.C2 = c.C2; fin.ldc2 = std::max(p, 1);
+  fin.Rh = c.Rh; fin.Rp = c.Rp;
+  fin.Rfull = Rdev; fin.ldR = ldR; fin.p = p; fin.col0 = col0;
+  if (p > 0) {
+    // P4: W = W R'^{-1}; C2 = Q^T W
+    {
+      RowPass r;
+      r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
+      r.Tri = c.Rp; r.write_y = 1; r.acc_x = 1;
+      r.epi.op = EPI_STORE; r.epi.out = c.C2; r.epi.out_ld = p;
+      RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+    }
+    // P5: W = W - Q C2; R2 = chol(W^T W); assemble R
+    {
+      RowPass r;
+      r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
+      r.C = c.C2; r.write_y = 1; r.acc_y = 1;
+      r.epi = fin;
+      RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+    }
+  } else {
+    // no previous basis: W = W R'^{-1} and its Gram in one pass
+    RowPass r;
+    r.n = n; r.Y = W; r.ldy = ldw; r.b = k;
+    r.Tri = c.Rp; r.write_y = 1; r.acc_y = 1;
+    r.epi = fin;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  // P6: Q_j = W R2^{-1}
+  RowPass r;
+  r.n = n; r.Y = W; r.ldy = ldw; r.b = k;
+  r.Tri = c.R2; r.write_y = 1;
+  return rowpass_launch(r, c.ar, c.st, &c.launches);
+}
+
+// ---- two-stage (Sections 6-7) -----------------------------------------------------------
+// Per panel j of a big panel with P finished columns Q:
+//   T1  C1_j = Q^T V_j
+//   T2  Vh_j = V_j - Q C1_j ; v_j = S Vh_j ; sketched BCGS2-HH -> T(:, j), q_j
+//   T3  Qbar_j = (Vh_j - Qbar_{<j} T_{<j,j}) T_jj^{-1} ; block column of G_B = Qbar^T Qbar
+// At the end of the big panel (R' = chol(G_B) from the last T3):
+//   T4  Qh = Qbar R'^{-1} ; C2 = Q^T Qh
+//   T5  W = Qh - Q C2 ; R2 = chol(W^T W) ; R_QB = C1 + C2 R' T, R_BB = R2 R' T
+//   T6  Q_B = W R2^{-1}
+int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
+  const int K = bp.K, cols = bp.cols, P = bp.P;
+  if (cols + k > K || P > c.pmax || K > c.kmax) return RBO_ERR_ARG;
+  double* W = bp.VB + (int64_t)cols * bp.ldv;
+  if (P > 0) {
+    RowPass r;
+    r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
+    r.acc_x = 1;
+    r.mixed = c.mixed;
+    r.epi.op = EPI_STORE; r.epi.out = c.C1; r.epi.out_ld = P; r.epi.col_off = cols;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  {
+    RowPass r;
+    r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
+    if (P > 0) { r.C = c.C1 + (size_t)cols * P; r.ldc = P; r.write_y = 1; }
+    r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed;
+    r.mixed = c.mixed;
+    r.epi.op = EPI_SKB2; r.epi.qs = c.qs; r.epi.T = c.T; r.epi.K = K; r.epi.poff = cols;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  {
+    RowPass r;
+    r.n = bp.n; r.X = bp.VB; r.ldx = bp.ldv; r.a = cols; r.Y = W; r.ldy = bp.ldv; r.b = k;
+    if (cols > 0) { r.C = c.T + (size_t)cols * K; r.ldc = K; r.acc_x = 1; }
+    r.Tri = c.T + cols + (size_t)cols * K; r.ldtri = K;
+    r.write_y = 1; r.acc_y = 1;
+    r.epi.op = EPI_GB; r.epi.GB = c.GB; r.epi.K = K; r.epi.poff = cols;
+    r.epi.last = (cols + k == K) ? 1 : 0;
+    r.epi.out_rp = c.Rp; r.epi.block = bp.blk;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  bp.cols += k;
+  return RBO_OK;
+}
+
+int bigpanel_finish(OrthCtx& c, BigPanel& bp, double* Rdev, int ldR, int col0, double* coords,
+                    int ldcoords) {
+  const int K = bp.K, P = bp.P;
+  if (bp.cols != K) return RBO_ERR_ARG;
+  Epilogue fin;
+  fin.op = EPI_CHOL; fin.out_r = c.R2; fin.stage = RBO_STAGE_FINAL; fin.block = bp.blk;
+  fin.asm_op = ASM_TWO_STAGE;
+  fin.C1 = c.C1; fin.ldc1 = std::max(P, 1);
+  fin.C2 = c.C2; fin.ldc2 = std::max(P, 1);
+  fin.Rh = c.T; fin.Rp = c.Rp;
+  fin.Rfull = Rdev; fin.ldR = ldR; fin.p = P; fin.col0 = col0;
+  fin.coords = coords; fin.ldcoords = ldcoords;
+  if (P > 0) {
+    {
+      RowPass r;
+      r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
+      r.Tri = c.Rp; r.write_y = 1; r.acc_x = 1;
+      r.epi.op = EPI_STORE; r.epi.out = c.C2; r.epi.out_ld = P;
+      RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+    }
+    {
+      RowPass r;
+      r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
+      r.C = c.C2; r.write_y = 1; r.acc_y = 1;
+      r.epi = fin;
+      RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+    }
+  } else {
+    RowPass r;
+    r.n = bp.n; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
+    r.Tri = c.Rp; r.write_y = 1; r.acc_y = 1;
+    r.epi = fin;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  }
+  RowPass r;
+  r.n = bp.n; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
+  r.Tri = c.R2; r.write_y = 1;
+  return rowpass_launch(r, c.ar, c.st, &c.launches);
+}
+
+}  // namespace rbo

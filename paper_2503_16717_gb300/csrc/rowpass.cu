@@ -1,0 +1,737 @@
+// The row pass: one fused streaming pass over the rows of a tall-skinny panel.
+//
+// Every step of the block orthogonalization that touches n-row data is an
+// instance of this kernel (BCGS Gram and update, sketch apply, the TRSMs of
+// CholQR/RandHH, the forward substitution of RandBCGS2 and the Gram matrices
+// feeding the Cholesky factorisations; Sections 4-7 of the paper):
+//
+//   per row r:   y'_r = (y_r - x_r C) Tri^{-1}      (or y_r Tri^{-1} - x_r C)
+//                write y'_r back to Y                     (optional)
+//                Z   += [x_r, y'_r]^T y'_r                (X^T Y' and/or Y'^T Y')
+//                SK  += s_r y'_r  (sketch column s_r: zeta entries +-1, hashed)
+//
+// Row tiles of T rows are staged in shared memory by the bulk-copy (TMA) engine
+// (cp.async.bulk + mbarrier, double buffered; ragged tiles use plain loads).
+// Each CTA owns a fixed set of tiles, keeps its partial Z in registers (one
+// output per thread slot) and its partial sketch in per-warp shared copies, then
+// writes one partial.  A two-level ticketed tree (groups of 16 CTAs, then one
+// top reducer) sums the partials in a fixed order, so results are bitwise
+// reproducible; the last CTA runs the small dense epilogue (Cholesky, Householder,
+// sketched BCGS2-HH, R assembly) on the reduced values.
+#include <algorithm>
+#include <map>
+
+#include "device_common.cuh"
+#include "small_dense.cuh"
+
+namespace rbo {
+
+constexpr int MAXO = 32;      // Z outputs per thread
+constexpr int GROUP = 16;     // CTAs per first-level reduction group
+constexpr int NST = 2;        // pipeline stages
+
+struct PassDev {
+  RowPass p;
+  int T;              // rows per tile
+  int ntiles;
+  int use_bulk;       // X/Y aligned for 16-byte bulk copies
+  int zr, no;         // Z rows, Z outputs (zr * b)
+  int L;              // partial length (no + d*b)
+  int nsw;            // sketch warps (copies)
+  int ngroups;
+  double* partials;
+  double* gpart;
+  unsigned* tickets;
+  DevStatus* status;
+  // shared memory layout (byte offsets from the dynamic base)
+  int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_red;
+};
+
+// ------------------------------------------------------------------------------------
+// epilogue pieces
+// ------------------------------------------------------------------------------------
+
+// M = A * B for upper-triangular k x k matrices (ld k), all in global or shared memory.
+__device__ void tri_mult(const double* A, const double* B, int k, double* M) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    int i = e % k, c = e / k;
+    double s = 0.0;
+    for (int l = i; l <= c; ++l) s += A[i + l * k] * B[l + c * k];
+    M[e] = (i <= c) ? s : 0.0;
+  }
+  __syncthreads();
+}
+
+// R assembly after the final Cholesky of a block (R2 in shared memory, k x k).
+__device__ void assemble(const Epilogue& e, const double* R2, int k, double* scratch) {
+  if (e.asm_op == ASM_NONE) return;
+  double* Rf = e.Rfull;
+  const int ld = e.ldR, p = e.p, c0 = e.col0;
+  if (e.asm_op == ASM_DIAG) {
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+      int i = t % k, c = t / k;
+      Rf[(p + i) + (size_t)(c0 + c) * ld] = R2[t];
+    }
+    __syncthreads();
+    return;
+  }
+  // M = R' * (R_hat or T)
+  double* M = scratch;  // k x k
+  tri_mult(e.Rp, e.Rh, k, M);
+  // R_jj = R2 M
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int i = t % k, c = t / k;
+    double s = 0.0;
+    for (int l = i; l <= c; ++l) s += R2[i + l * k] * M[l + c * k];
+    Rf[(p + i) + (size_t)(c0 + c) * ld] = (i <= c) ? s : 0.0;
+  }
+  // R_top = C1 + C2 M
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
+    int i = t % p, c = t / p;
+    double s = e.C1[i + (size_t)c * e.ldc1];
+    for (int l = 0; l <= c; ++l) s += e.C2[i + (size_t)l * e.ldc2] * M[l + c * k];
+    Rf[i + (size_t)(c0 + c) * ld] = s;
+  }
+  if (e.asm_op == ASM_TWO_STAGE && e.coords != nullptr) {
+    // coordinates of Qbar_B in [Q, Q_B]: [C2 R'; R2 R']
+    for (int t = threadIdx.x; t < (p + k) * k; t += blockDim.x) {
+      int i = t % (p + k), c = t / (p + k);
+      double s = 0.0;
+      if (i < p) {
+        for (int l = 0; l <= c; ++l) s += e.C2[i + (size_t)l * e.ldc2] * e.Rp[l + c * k];
+      } else {
+        int ii = i - p;
+        for (int l = ii; l <= c; ++l) s += R2[ii + l * k] * e.Rp[l + c * k];
+      }
+      e.coords[i + (size_t)c * e.ldcoords] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// The small dense work of the last CTA.  `red` holds the reduced partial
+// (Z: zr x b as o = i*b + c, then the sketch d x b column-major); `sm` is free
+// shared memory.
+__device__ void run_epilogue(const PassDev& P, const double* red, double* sm, int* s_flag) {
+  const RowPass& rp = P.p;
+  const Epilogue& e = rp.epi;
+  const int b = rp.b;
+  const int ax = rp.acc_x ? rp.a : 0;
+  switch (e.op) {
+    case EPI_STORE: {
+      for (int t = threadIdx.x; t < ax * b; t += blockDim.x) {
+        int i = t / b, c = t % b;
+        e.out[(e.row_off + i) + (size_t)(e.col_off + c) * e.out_ld] = red[t];
+      }
+      break;
+    }
+    case EPI_STORE_ALL: {
+      for (int t = threadIdx.x; t < P.zr * b; t += blockDim.x) {
+        int i = t / b, c = t % b;
+        e.out[i + (size_t)c * P.zr] = red[t];
+      }
+      if (e.out_sk != nullptr)
+        for (int t = threadIdx.x; t < rp.sk_d * b; t += blockDim.x) e.out_sk[t] = red[P.no + t];
+      break;
+    }
+    case EPI_CHOL: {
+      double* G = sm;  // b x b
+      for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        int i = t % b, c = t / b;
+        G[t] = red[(ax + i) * b + c];
+      }
+      __syncthreads();
+      int bad = cta_cholesky(G, b, s_flag);
+      if (bad >= 0) {
+        if (threadIdx.x == 0) set_breakdown(P.status, e.block, bad, e.stage);
+        return;
+      }
+      if (e.out_r != nullptr)
+        for (int t = threadIdx.x; t < b * b; t += blockDim.x) e.out_r[t] = G[t];
+      __syncthreads();
+      assemble(e, G, b, sm + b * b);
+      break;
+    }
+    case EPI_HH: {
+      const int d = rp.sk_d;
+      double* A = sm;                      // d x b
+      double* R = A + (size_t)d * b;       // b x b
+      double* beta = R + b * b;            // b
+      double* sg = beta + b;               // b
+      double* scr = sg + b;                // 32
+      for (int t = threadIdx.x; t < d * b; t += blockDim.x) A[t] = red[P.no + t];
+      __syncthreads();
+      cta_householder(A, d, b, R, nullptr, beta, sg, scr);
+      for (int t = threadIdx.x; t < b * b; t += blockDim.x) e.out_r[t] = R[t];
+      break;
+    }
+    case EPI_SKB2: {
+      // sketched BCGS2 with Householder intra step (Section 7.2)
+      const int d = rp.sk_d, k = b, pp = e.poff, K = e.K;
+      double* v = sm;                       // d x k
+      double* A = v + (size_t)d * k;        // d x k (Householder work)
+      double* Qn = A + (size_t)d * k;       // d x k
+      double* c1 = Qn + (size_t)d * k;      // pp x k
+      double* c2 = c1 + (size_t)pp * k;     // pp x k
+      double* R = c2 + (size_t)pp * k;      // k x k
+      double* beta = R + k * k;
+      double* sg = beta + k;
+      double* scr = sg + k;
+      for (int t = threadIdx.x; t < d * k; t += blockDim.x) v[t] = red[P.no + t];
+      __syncthreads();
+      if (pp > 0) {
+        cta_gemm_tn(e.qs, d, v, d, pp, k, c1);
+        cta_gemm_nn_sub(e.qs, d, c1, d, pp, k, v);
+        cta_gemm_tn(e.qs, d, v, d, pp, k, c2);
+        cta_gemm_nn_sub(e.qs, d, c2, d, pp, k, v);
+        for (int t = threadIdx.x; t < pp * k; t += blockDim.x) {
+          int i = t % pp, c = t / pp;
+          e.T[i + (size_t)(pp + c) * K] = c1[t] + c2[t];
+        }
+      }
+      for (int t = threadIdx.x; t < d * k; t += blockDim.x) A[t] = v[t];
+      __syncthreads();
+      cta_householder(A, d, k, R, Qn, beta, sg, scr);
+      for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        int i = t % k, c = t / k;
+        e.T[(pp + i) + (size_t)(pp + c) * K] = R[t];
+      }
+      for (int t = threadIdx.x; t < d * k; t += blockDim.x) {
+        int r = t % d, c = t / d;
+        e.qs[r + (size_t)(pp + c) * d] = Qn[t];
+      }
+      break;
+    }
+    case EPI_GB: {
+      // block column [Qbar_prev, Qbar_j]^T Qbar_j of the big-panel Gram G_B
+      const int K = e.K, pp = e.poff;
+      for (int t = threadIdx.x; t < P.zr * b; t += blockDim.x) {
+        int i = t / b, c = t % b;
+        e.GB[i + (size_t)(pp + c) * K] = red[t];
+      }
+      __threadfence_block();
+      __syncthreads();
+      if (e.last) {
+        const int Kc = pp + b;  // columns of the big panel
+        double* G = sm;
+        for (int t = threadIdx.x; t < Kc * Kc; t += blockDim.x) {
+          int i = t % Kc, c = t / Kc;
+          G[t] = (i <= c) ? e.GB[i + (size_t)c * K] : 0.0;
+        }
+        __syncthreads();
+        int bad = cta_cholesky(G, Kc, s_flag);
+        if (bad >= 0) {
+          if (threadIdx.x == 0) set_breakdown(P.status, e.block, bad, RBO_STAGE_BIGPANEL);
+          return;
+        }
+        for (int t = threadIdx.x; t < Kc * Kc; t += blockDim.x) e.out_rp[t] = G[t];
+      }
+      break;
+    }
+    default:
+      break;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------
+// the kernel
+// ------------------------------------------------------------------------------------
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ PassDev P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_flag;
+  __shared__ int s_last;
+  const RowPass& rp = P.p;
+  if (read_code(P.status) != 0) return;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = P.T, a = rp.a, b = rp.b;
+  const int ax = rp.acc_x ? a : 0;
+  const int64_t n = rp.n;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  double* Cs = reinterpret_cast<double*>(smem + P.off_c);
+  double* Ts = reinterpret_cast<double*>(smem + P.off_tri);
+  double* dinv = reinterpret_cast<double*>(smem + P.off_dinv);
+  double* skd = reinterpret_cast<double*>(smem + P.off_sk);
+  float* skf = reinterpret_cast<float*>(smem + P.off_sk);
+  const int d = rp.sk_d;
+  const bool do_sk = d > 0;
+
+  // small matrices + sketch copies
+  if (rp.C) {
+    const int ldc = rp.ldc > 0 ? rp.ldc : a;
+    for (int t = tid; t < a * b; t += NT) Cs[t] = rp.C[(t % a) + (size_t)(t / a) * ldc];
+  }
+  if (rp.Tri) {
+    const int ldt = rp.ldtri > 0 ? rp.ldtri : b;
+    for (int t = tid; t < b * b; t += NT) {
+      const int i = t % b, c = t / b;
+      Ts[t] = (i <= c) ? rp.Tri[i + (size_t)c * ldt] : 0.0;
+    }
+    for (int t = tid; t < b; t += NT) dinv[t] = 1.0 / rp.Tri[t + (size_t)t * ldt];
+  }
+  if (do_sk) {
+    const int tot = P.nsw * d * b;
+    if (MIXED)
+      for (int t = tid; t < tot; t += NT) skf[t] = 0.0f;
+    else
+      for (int t = tid; t < tot; t += NT) skd[t] = 0.0;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // per-thread Z outputs
+  double acc[MAXO];
+  float accf[MAXO];
+#pragma unroll
+  for (int j = 0; j < MAXO; ++j) {
+    acc[j] = 0.0;
+    accf[j] = 0.0f;
+  }
+
+  const int ncol_tile = (a + b);
+  auto stage_X = [&](int s) {
+    return reinterpret_cast<double*>(smem + P.off_stage + (size_t)s * P.stage_bytes);
+  };
+  auto stage_Y = [&](int s) { return stage_X(s) + (size_t)a * T; };
+
+  // bulk-copy a full tile into stage s (thread 0 only)
+  auto issue_tile = [&](int tile, int s) {
+    const int64_t r0 = (int64_t)tile * T;
+    double* xs = stage_X(s);
+    double* ys = stage_Y(s);
+    const uint32_t bytes = (uint32_t)T * 8u;
+    mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile);
+    for (int i = 0; i < a; ++i) bulk_copy_g2s(xs + (size_t)i * T, rp.X + i * rp.ldx + r0, bytes, &bars[s]);
+    for (int c = 0; c < b; ++c) bulk_copy_g2s(ys + (size_t)c * T, rp.Y + c * rp.ldy + r0, bytes, &bars[s]);
+  };
+  auto bulk_ok = [&](int tile) {
+    return P.use_bulk && ((int64_t)(tile + 1) * T <= n);
+  };
+
+  uint32_t phase[NST] = {0u, 0u};
+  int first = blockIdx.x;
+  if (first < P.ntiles && bulk_ok(first) && tid == 0) issue_tile(first, 0);
+
+  int it = 0;
+  bool timed_out = false;
+  for (int tile = first; tile < P.ntiles; tile += gridDim.x, ++it) {
+    const int s = it & 1;
+    const int64_t r0 = (int64_t)tile * T;
+    const int rows = (n - r0 < (int64_t)T) ? (int)(n - r0) : T;
+    double* xs = stage_X(s);
+    double* ys = stage_Y(s);
+    if (bulk_ok(tile)) {
+      if (!mbar_wait_bounded(&bars[s], phase[s])) {
+        timed_out = true;
+      }
+      phase[s] ^= 1u;
+    } else {
+      // ragged or unaligned tile: plain coalesced loads with zero fill
+      for (int t = tid; t < ncol_tile * T; t += NT) {
+        int col = t / T, r = t % T;
+        double v = 0.0;
+        if (r < rows) v = (col < a) ? rp.X[col * rp.ldx + r0 + r] : rp.Y[(col - a) * rp.ldy + r0 + r];
+        xs[t] = v;  // X and Y stages are contiguous
+      }
+      __syncthreads();
+    }
+    if (timed_out) {
+      if (tid == 0) set_error(P.status, RBO_ERR_TIMEOUT, 1);
+      return;
+    }
+    // prefetch the next tile of this CTA into the other stage
+    const int nxt = tile + gridDim.x;
+    if (tid == 0 && nxt < P.ntiles && bulk_ok(nxt)) {
+      fence_proxy_async();
+      issue_tile(nxt, s ^ 1);
+    }
+
+    // ---- phase A: y' = transform(y), in place in the Y stage --------------------
+    const int tpr = NT / T;          // threads per row
+    const int r = tid % T, q = tid / T;
+    auto tri_solve = [&]() {
+      if (q == 0) {
+        for (int c = 0; c < b; ++c) {
+          double v = ys[c * T + r];
+          for (int i = 0; i < c; ++i) v = fma(-ys[i * T + r], Ts[i + c * b], v);
+          ys[c * T + r] = v * dinv[c];
+        }
+      }
+    };
+    auto project = [&]() {
+      for (int c = q; c < b; c += tpr) {
+        double v = ys[c * T + r];
+        for (int i = 0; i < a; ++i) v = fma(-xs[i * T + r], Cs[i + c * a], v);
+        ys[c * T + r] = v;
+      }
+    };
+    if (rp.Tri && rp.tri_first) {
+      tri_solve();
+      __syncthreads();
+    }
+    if (rp.C) {
+      project();
+      __syncthreads();
+    }
+    if (rp.Tri && !rp.tri_first) {
+      tri_solve();
+      __syncthreads();
+    }
+    if (rp.write_y) {
+      for (int t = tid; t < b * T; t += NT) {
+        int c = t / T, rr = t % T;
+        if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = ys[t];
+      }
+    }
+
+    // ---- phase B: Gram outputs Z = [X, Y']^T Y' --------------------------------
+    if (MIXED && (P.no > 0 || do_sk)) {
+      // float32 copies of the tile (integer-ALU conversion) in place: the float for
+      // element t sits in the first 4 bytes of its double slot
+      __syncthreads();
+      for (int t = tid; t < ncol_tile * T; t += NT) {
+        float f = f64_to_f32_int(xs[t]);
+        reinterpret_cast<float*>(xs + t)[0] = f;
+      }
+      __syncthreads();
+    }
+    if (P.no > 0) {
+      if (MIXED) {
+#pragma unroll
+        for (int j = 0; j < MAXO; ++j) {
+          const int o = tid + j * NT;
+          if (o < P.no) {
+            const int i = o / b, c = o % b;
+            const double* zsrc = (i < ax) ? xs + (size_t)i * T : ys + (size_t)(i - ax) * T;
+            const double* ysrc = ys + (size_t)c * T;
+            float sacc = accf[j];
+            for (int rr = 0; rr < T; ++rr)
+              sacc = fmaf(reinterpret_cast<const float*>(zsrc + rr)[0],
+                          reinterpret_cast<const float*>(ysrc + rr)[0], sacc);
+            accf[j] = sacc;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < MAXO; ++j) {
+          const int o = tid + j * NT;
+          if (o < P.no) {
+            const int i = o / b, c = o % b;
+            const double* zsrc = (i < ax) ? xs + (size_t)i * T : ys + (size_t)(i - ax) * T;
+            const double* ysrc = ys + (size_t)c * T;
+            double sacc = acc[j];
+            for (int rr = 0; rr < T; ++rr) sacc = fma(zsrc[rr], ysrc[rr], sacc);
+            acc[j] = sacc;
+          }
+        }
+      }
+    }
+    // ---- phase B': sketch S Y' (warp-private copies, lane-ordered collisions) -----
+    if (do_sk && warp < P.nsw) {
+      const int rr = warp * 32 + lane;
+      const bool valid = rr < rows && rr < T;
+      int idx[ZMAX], neg[ZMAX];
+#pragma unroll
+      for (int t = 0; t < ZMAX; ++t) {
+        idx[t] = 0;
+        neg[t] = 0;
+      }
+      if (valid) {
+        if (!sketch_column(rp.sk_seed, (uint64_t)(r0 + rr), d, rp.sk_zeta, idx, neg))
+          set_error(P.status, RBO_ERR_SKETCH, 2);
+      }
+      const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+      for (int t = 0; t < ZMAX; ++t) {
+        if (t < rp.sk_zeta) {
+          const int key = valid ? idx[t] : -1 - lane;
+          const unsigned grp = __match_any_sync(0xffffffffu, key);
+          const int rank = __popc(grp & lt_mask);
+          const int maxrank = __reduce_max_sync(0xffffffffu, (unsigned)rank);
+          for (int kk = 0; kk <= maxrank; ++kk) {
+            if (valid && rank == kk) {
+              if (MIXED) {
+                float* cp = skf + (size_t)warp * d * b;
+                for (int c = 0; c < b; ++c) {
+                  float yv = reinterpret_cast<const float*>(ys + (size_t)c * T + rr)[0];
+                  cp[idx[t] + c * d] += neg[t] ? -yv : yv;
+                }
+              } else {
+                double* cp = skd + (size_t)warp * d * b;
+                for (int c = 0; c < b; ++c) {
+                  double yv = ys[(size_t)c * T + rr];
+                  cp[idx[t] + c * d] += neg[t] ? -yv : yv;
+                }
+              }
+            }
+            __syncwarp();
+          }
+        }
+      }
+    }
+    __syncthreads();  // stage s free for reuse
+  }
+
+  // ---------------- partials + fixed-order two-level tree -------------------------
+  if (P.L == 0) return;
+  double* mypart = P.partials + (size_t)blockIdx.x * P.L;
+#pragma unroll
+  for (int j = 0; j < MAXO; ++j) {
+    const int o = tid + j * NT;
+    if (o < P.no) mypart[o] = MIXED ? (double)accf[j] : acc[j];
+  }
+  if (do_sk) {
+    for (int t = tid; t < d * b; t += NT) {
+      double s = 0.0;
+      for (int w = 0; w < P.nsw; ++w)
+        s += MIXED ? (double)skf[(size_t)w * d * b + t] : skd[(size_t)w * d * b + t];
+      mypart[P.no + t] = s;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  const int g = blockIdx.x / GROUP;
+  const int gsize = min(GROUP, (int)gridDim.x - g * GROUP);
+  if (tid == 0) {
+    unsigned prev = atomicAdd(&P.tickets[g], 1u);
+    s_last = (prev == (unsigned)(gsize - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  {
+    const double* base = P.partials + (size_t)g * GROUP * P.L;
+    double* gout = P.gpart + (size_t)g * P.L;
+    for (int t = tid; t < P.L; t += NT) {
+      double s = 0.0;
+      for (int i = 0; i < gsize; ++i) s += __ldcg(base + (size_t)i * P.L + t);
+      gout[t] = s;
+    }
+  }
+  if (tid == 0) P.tickets[g] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned prev = atomicAdd(&P.tickets[P.ngroups], 1u);
+    s_last = (prev == (unsigned)(P.ngroups - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double* red = reinterpret_cast<double*>(smem + P.off_red);
+  for (int t = tid; t < P.L; t += NT) {
+    double s = 0.0;
+    for (int i = 0; i < P.ngroups; ++i) s += __ldcg(P.gpart + (size_t)i * P.L + t);
+    red[t] = s;
+  }
+  if (tid == 0) P.tickets[P.ngroups] = 0u;
+  __syncthreads();
+  double* sm = red + ((P.L + 1) & ~1);
+  run_epilogue(P, red, sm, &s_flag);
+}
+
+// ------------------------------------------------------------------------------------
+// host launcher
+// ------------------------------------------------------------------------------------
+static int g_num_sms = 0;
+static std::map<long long, int> g_occ;
+
+static int sm_count() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+static int g_smem_max[2] = {0, 0};
+
+// Largest dynamic shared memory of the row-pass kernel (opt-in limit minus its
+// static shared memory); raises the kernel's limit to it on first use.
+template <bool MIXED>
+static int smem_limit() {
+  int& lim = g_smem_max[MIXED ? 1 : 0];
+  if (lim == 0) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    size_t stat = 0;
+    if (cudaFuncGetAttributes(&fa, rowpass_kernel<MIXED>) == cudaSuccess) stat = fa.sharedSizeBytes;
+    lim = optin - (int)stat - 64;
+    if (cudaFuncSetAttribute(rowpass_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             lim) != cudaSuccess) {
+      cudaGetLastError();
+      lim = 48 * 1024 - (int)stat;
+    }
+  }
+  return lim;
+}
+
+template <bool MIXED>
+static int occupancy(int smem) {
+  long long key = (long long)smem * 2 + (MIXED ? 1 : 0);
+  auto it = g_occ.find(key);
+  if (it != g_occ.end()) return it->second;
+  int nb = 0;
+  smem_limit<MIXED>();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<MIXED>, NT, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  if (nb < 1) nb = 1;
+  g_occ[key] = nb;
+  return nb;
+}
+
+// shared memory bytes of the small dense epilogue (beyond the reduced vector)
+static size_t epilogue_doubles(const RowPass& rp, int zr) {
+  const int b = rp.b, d = rp.sk_d;
+  const Epilogue& e = rp.epi;
+  size_t need = 0;
+  switch (e.op) {
+    case EPI_CHOL: need = (size_t)b * b * 2 + 64; break;
+    case EPI_HH: need = (size_t)d * b + (size_t)b * b + 2 * b + 64; break;
+    case EPI_SKB2: need = (size_t)3 * d * b + (size_t)2 * e.poff * b + (size_t)b * b + 2 * b + 64; break;
+    case EPI_GB: need = (size_t)(e.poff + b) * (e.poff + b) + 64; break;
+    default: break;
+  }
+  (void)zr;
+  return need;
+}
+
+int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launches) {
+  RowPass rp = rpin;
+  if (rp.n <= 0 || rp.b <= 0 || rp.b > 64 || rp.a < 0 || rp.a > 128) return RBO_ERR_ARG;
+  if (rp.a > 0 && rp.X == nullptr) return RBO_ERR_ARG;
+  if (rp.a == 0) { rp.C = nullptr; rp.acc_x = 0; }
+  if (rp.sk_d > DMAX || rp.sk_zeta > ZMAX) return RBO_ERR_ARG;
+  const int zr = (rp.acc_x ? rp.a : 0) + (rp.acc_y ? rp.b : 0);
+  const int no = zr * rp.b;
+  if (no > MAXO * NT) return RBO_ERR_ARG;
+  const int dsk = rp.sk_d > 0 ? rp.sk_d : 0;
+  const int L = no + dsk * rp.b;
+  const int mixed = rp.mixed ? 1 : 0;
+
+  // choose the tile height: largest of 64/32 that fits
+  int T = 64;
+  size_t smem = 0;
+  int nsw = 0;
+  size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_sk = 0, off_red = 0;
+  for (;;) {
+    nsw = dsk > 0 ? std::max(1, T / 32) : 0;
+    off_stage = 64;
+    stage_bytes = (size_t)(rp.a + rp.b) * T * 8;
+    size_t o = off_stage + NST * stage_bytes;
+    off_c = o; o += (rp.C ? (size_t)rp.a * rp.b * 8 : 0);
+    off_tri = o; o += (rp.Tri ? (size_t)rp.b * rp.b * 8 : 0);
+    off_dinv = o; o += (rp.Tri ? (size_t)rp.b * 8 : 0);
+    o = (o + 15) & ~size_t(15);
+    off_sk = o; o += (size_t)nsw * dsk * rp.b * (mixed ? 4 : 8);
+    size_t loop_bytes = o;
+    off_red = 64;
+    size_t epi_bytes = off_red + ((size_t)L + 2) * 8 + epilogue_doubles(rp, zr) * 8;
+    smem = std::max(loop_bytes, epi_bytes);
+    if (smem <= 220 * 1024 || T == 16) break;
+    T /= 2;
+  }
+  const int limit = mixed ? smem_limit<true>() : smem_limit<false>();
+  if ((long long)smem > limit) return RBO_ERR_ARG;
+  const int ntiles = (int)((rp.n + T - 1) / T);
+  const int occ = mixed ? occupancy<true>((int)smem) : occupancy<false>((int)smem);
+  int G = std::min(ntiles, occ * sm_count());
+  if (G < 1) G = 1;
+  const int ngroups = (G + GROUP - 1) / GROUP;
+
+  PassDev P;
+  P.p = rp;
+  P.T = T;
+  P.ntiles = ntiles;
+  const bool alignedX = rp.a == 0 || (((uintptr_t)rp.X & 15) == 0 && (rp.ldx % 2) == 0);
+  const bool alignedY = (((uintptr_t)rp.Y & 15) == 0 && (rp.ldy % 2) == 0);
+  P.use_bulk = (alignedX && alignedY) ? 1 : 0;
+  P.zr = zr;
+  P.no = no;
+  P.L = L;
+  P.nsw = nsw;
+  P.ngroups = ngroups;
+  P.status = ar->status;
+  P.off_stage = (int)off_stage;
+  P.stage_bytes = (int)stage_bytes;
+  P.off_c = (int)off_c;
+  P.off_tri = (int)off_tri;
+  P.off_dinv = (int)off_dinv;
+  P.off_sk = (int)off_sk;
+  P.off_red = (int)off_red;
+  P.partials = nullptr;
+  P.gpart = nullptr;
+  P.tickets = nullptr;
+  if (L > 0) {
+    // reduction scratch reserved for the whole call (stream-ordered reuse); the
+    // tickets were zeroed at the start of the call and every tree resets its own
+    const size_t need = ((size_t)G * L + (size_t)ngroups * L) * 8;
+    if (ar->red == nullptr || need > ar->red_bytes) return RBO_ERR_NOMEM;
+    if (ngroups + 1 > ar->n_tickets) return RBO_ERR_NOMEM;
+    P.partials = ar->red;
+    P.gpart = ar->red + (size_t)G * L;
+    P.tickets = ar->tickets;
+  }
+  ProfToken tok = prof_start(st);
+  if (mixed)
+    rowpass_kernel<true><<<G, NT, smem, st>>>(P);
+  else
+    rowpass_kernel<false><<<G, NT, smem, st>>>(P);
+  if (prof_on()) {
+    // algorithmic traffic: every n-row column read once, written once
+    const double nn = (double)rp.n, A = rp.a, B = rp.b;
+    const bool readx = rp.a > 0 && (rp.acc_x || rp.C);
+    const double by = 8.0 * nn * ((readx ? A : 0.0) + B + (rp.write_y ? B : 0.0));
+    double fl = 0.0;
+    if (rp.C) fl += 2.0 * nn * A * B;                        // projection
+    if (rp.Tri) fl += nn * B * B;                             // triangular solve
+    if (rp.acc_x) fl += 2.0 * nn * A * B;                     // X^T Y'
+    if (rp.acc_y) fl += nn * B * (B + 1.0);                   // Y'^T Y' (symmetric)
+    if (rp.sk_d > 0) fl += nn * (double)rp.sk_zeta * B;       // sketch accumulation
+    prof_stop(tok, st, 0, by, fl);
+  }
+  if (launches) ++*launches;
+  return note_cuda(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------------------------
+// sketch entries (tests / bit-exactness)
+// ------------------------------------------------------------------------------------
+__global__ void sketch_entries_kernel(int64_t row0, int64_t nrows, int d, int zeta, uint64_t seed,
+                                      int32_t* idx, int8_t* sign, DevStatus* status) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int ix[ZMAX], ng[ZMAX];
+#pragma unroll
+  for (int t = 0; t < ZMAX; ++t) { ix[t] = 0; ng[t] = 0; }
+  if (!sketch_column(seed, (uint64_t)(row0 + r), d, zeta, ix, ng)) set_error(status, RBO_ERR_SKETCH, 3);
+#pragma unroll
+  for (int t = 0; t < ZMAX; ++t) {
+    if (t < zeta) {
+      idx[r * zeta + t] = ix[t];
+      sign[r * zeta + t] = ng[t] ? (int8_t)-1 : (int8_t)1;
+    }
+  }
+}
+
+int sketch_entries_launch(int64_t row0, int64_t nrows, int d, int zeta, uint64_t seed, int32_t* idx,
+                          int8_t* sign, DevStatus* status, cudaStream_t st) {
+  if (nrows <= 0) return RBO_OK;
+  int64_t blocks = (nrows + 255) / 256;
+  sketch_entries_kernel<<<(unsigned)blocks, 256, 0, st>>>(row0, nrows, d, zeta, seed, idx, sign, status);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+}  // namespace rbo

@@ -1,0 +1,177 @@
+// CSR sparse kernels of the matrix-powers kernel (Section 4) and the small vector
+// kernels of the GMRES driver.
+//
+// SpMV: a group of LPR lanes per row (LPR = 4 for stencil-like rows of ~7
+// entries, 8/32 for denser rows); the lanes of a group read consecutive entries
+// of the row (coalesced col/val streams) and combine with shuffles in a fixed
+// order, so the result is deterministic.  The optional diagonal scaling D of the
+// right Jacobi preconditioner (A D x) is applied to the gathered x entries.
+#include "device_common.cuh"
+
+namespace rbo {
+
+// Entries with a column index outside [0, n), or rows whose pointers leave [0, nnz],
+// are skipped and reported through the status word (RBO_ERR_ARG) instead of being
+// dereferenced.
+template <int LPR>
+__global__ void __launch_bounds__(256) spmv_kernel(int64_t n, int64_t nnz,
+                                                   const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col,
+                                                   const double* __restrict__ val,
+                                                   const double* __restrict__ dscale,
+                                                   const double* __restrict__ x,
+                                                   const double* __restrict__ bvec,
+                                                   double* __restrict__ y, DevStatus* status) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gid / LPR;
+  const int sub = (int)(gid % LPR);
+  double s = 0.0;
+  if (row < n) {
+    int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+    if (beg < 0 || end < beg || (int64_t)end > nnz) {
+      if (status && sub == 0) set_error(status, RBO_ERR_ARG, 11);
+      end = beg;
+    }
+    for (int j = beg + sub; j < end; j += LPR) {
+      const int cj = __ldg(col + j);
+      if (cj < 0 || (int64_t)cj >= n) {
+        if (status) set_error(status, RBO_ERR_ARG, 12);
+        continue;
+      }
+      const double xv = dscale ? __ldg(dscale + cj) * __ldg(x + cj) : __ldg(x + cj);
+      s = fma(__ldg(val + j), xv, s);
+    }
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LPR);
+  if (row < n && sub == 0) y[row] = bvec ? (bvec[row] - s) : s;
+}
+
+static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
+                               const double* b, double* y, DevStatus* status, cudaStream_t st);
+
+template <int LPR>
+static void spmv_go(const CsrDev& A, const double* dscale, const double* x, const double* b,
+                    double* y, DevStatus* status, cudaStream_t st) {
+  const int64_t threads = A.n * LPR;
+  const int64_t blocks = (threads + 255) / 256;
+  spmv_kernel<LPR><<<(unsigned)blocks, 256, 0, st>>>(A.n, A.nnz, A.rowptr, A.col, A.val, dscale, x,
+                                                     b, y, status);
+}
+
+static int spmv_dispatch(const CsrDev& A, const double* dscale, const double* x, const double* b,
+                         double* y, DevStatus* status, cudaStream_t st) {
+  if (A.n <= 0) return RBO_OK;
+  ProfToken tok = prof_start(st);
+  int e = spmv_dispatch_inner(A, dscale, x, b, y, status, st);
+  // algorithmic bytes: values + column indices + row pointers, x and y once each
+  // (plus b and the scaling vector when used); 2 flops per stored entry
+  const double nn = (double)A.n, nz = (double)A.nnz;
+  prof_stop(tok, st, 1, 12.0 * nz + 4.0 * (nn + 1) + 16.0 * nn + (b ? 8.0 * nn : 0.0) +
+                            (dscale ? 8.0 * nn : 0.0), 2.0 * nz);
+  return e;
+}
+
+static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
+                               const double* b, double* y, DevStatus* status, cudaStream_t st) {
+  const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
+  if (avg <= 8.0)
+    spmv_go<4>(A, dscale, x, b, y, status, st);
+  else if (avg <= 24.0)
+    spmv_go<8>(A, dscale, x, b, y, status, st);
+  else
+    spmv_go<32>(A, dscale, x, b, y, status, st);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+int spmv_launch(const CsrDev& A, const double* dscale, const double* x, double* y, DevStatus* status,
+                cudaStream_t st) {
+  return spmv_dispatch(A, dscale, x, nullptr, y, status, st);
+}
+
+int residual_launch(const CsrDev& A, const double* b, const double* x, double* r, DevStatus* status,
+                    cudaStream_t st) {
+  return spmv_dispatch(A, nullptr, x, b, r, status, st);
+}
+
+__global__ void scale_columns_kernel(int64_t n, int64_t nnz, const int32_t* __restrict__ col,
+                                     const double* __restrict__ val, const double* __restrict__ ds,
+                                     double* __restrict__ out) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; j < nnz; j += stride) {
+    const int32_t c = col[j];
+    out[j] = (c >= 0 && (int64_t)c < n) ? val[j] * ds[c] : 0.0;
+  }
+}
+
+int scale_columns_launch(const CsrDev& A, const double* dscale, double* val_out, cudaStream_t st) {
+  if (A.nnz <= 0) return RBO_OK;
+  int64_t blocks = std::min<int64_t>((A.nnz + 255) / 256, 65535LL * 16);
+  scale_columns_kernel<<<(unsigned)blocks, 256, 0, st>>>(A.n, A.nnz, A.col, A.val, dscale, val_out);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+__global__ void jacobi_kernel(int64_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ col, const double* __restrict__ val,
+                              double* __restrict__ ds, DevStatus* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double dia = 0.0;
+  int beg = rowptr[i], end = rowptr[i + 1];
+  if (beg < 0 || end < beg || (int64_t)end > nnz) end = beg;
+  for (int j = beg; j < end; ++j)
+    if (col[j] == (int32_t)i) dia = val[j];
+  if (dia == 0.0) {
+    set_error(status, RBO_ERR_ARG, 10);
+    ds[i] = 0.0;
+  } else {
+    ds[i] = 1.0 / dia;
+  }
+}
+
+int jacobi_launch(const CsrDev& A, double* dscale, DevStatus* status, cudaStream_t st) {
+  if (A.n <= 0) return RBO_OK;
+  jacobi_kernel<<<(unsigned)((A.n + 255) / 256), 256, 0, st>>>(A.n, A.nnz, A.rowptr, A.col, A.val, dscale,
+                                                                status);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+// y += Q z: one thread per row, z in shared memory
+__global__ void gemv_update_kernel(int64_t n, int k, const double* __restrict__ Q, int64_t ldq,
+                                   const double* __restrict__ z, double* __restrict__ y) {
+  __shared__ double zs[256];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) zs[t] = z[t];
+  __syncthreads();
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < k; ++c) s = fma(Q[i + c * ldq], zs[c], s);
+  y[i] += s;
+}
+
+int gemv_update_launch(int64_t n, int k, const double* Q, int64_t ldq, const double* z, double* y,
+                       cudaStream_t st) {
+  if (n <= 0 || k <= 0) return RBO_OK;
+  if (k > 256) return RBO_ERR_ARG;
+  gemv_update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, k, Q, ldq, z, y);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+__global__ void scale_vec_kernel(int64_t n, const double* __restrict__ ds, const double* __restrict__ y,
+                                 double* __restrict__ x, int mode) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = y[i];
+  if (ds) v = mode == 0 ? v * ds[i] : v / ds[i];
+  x[i] = v;
+}
+
+int scale_vec_launch(int64_t n, const double* dscale, const double* y, double* x, int mode,
+                     cudaStream_t st) {
+  if (n <= 0) return RBO_OK;
+  scale_vec_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dscale, y, x, mode);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+}  // namespace rbo

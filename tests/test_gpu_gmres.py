@@ -1,0 +1,93 @@
+"""GPU parity of the matrix-powers kernel and s-step GMRES against the oracle.
+
+GMRES parity: converged to tol on the true residual, iteration count within one
+check granularity (s for one-stage, s_hat for two-stage) of the oracle's, and
+b = A*1 recovers x = 1."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import krylov
+
+pytestmark = pytest.mark.gpu
+
+
+def test_mpk_matches_oracle(rbo):
+    import torch
+    A = synth.poisson3d_csr(20)
+    Ad = rbo.DeviceCSR.from_host(A)
+    u = np.random.default_rng(0).standard_normal(A.n)
+    V = rbo.mpk_csr(Ad, torch.from_numpy(u).cuda(), 5)
+    ref = krylov.mpk(A.to_scipy(), u, 5)
+    got = V.cpu().numpy()
+    for i in range(5):
+        assert np.abs(got[:, i] - ref[:, i]).max() <= 1e-13 * np.abs(ref[:, i]).max()
+
+
+def test_mpk_jacobi_scaled(rbo):
+    import torch
+    A = synth.random_csr(3001, 9, seed=4)
+    Ad = rbo.DeviceCSR.from_host(A)
+    u = np.random.default_rng(1).standard_normal(A.n)
+    Ahat, dinv = krylov.jacobi_scaled(A)
+    V = rbo.mpk_csr(Ad, torch.from_numpy(u).cuda(), 3, dscale=torch.from_numpy(dinv).cuda())
+    ref = krylov.mpk(Ahat, u, 3)
+    assert np.allclose(V.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("N,s,s_hat,m", [(16, 5, 0, 30), (16, 5, 10, 30), (20, 5, 20, 60),
+                                         (12, 3, 0, 12)])
+def test_poisson_matches_oracle(rbo, N, s, s_hat, m):
+    import torch
+    A = synth.poisson3d_csr(N)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    x, info = rbo.sstep_gmres(Ad, torch.from_numpy(b).cuda(), s=s, s_hat=s_hat, m=m, tol=1e-10)
+    scheme = "two" if s_hat > s else "one"
+    ref = krylov.sstep_gmres(A, b, s=s, m=m, s_hat=(s_hat or None), scheme=scheme, tol=1e-10)
+    assert info["converged"] == 1 and ref.converged
+    gran = s_hat if s_hat > s else s
+    assert abs(info["iterations"] - ref.iterations) <= gran
+    xh = x.cpu().numpy()
+    r = b - A.to_scipy() @ xh
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    assert np.abs(xh - 1.0).max() <= 1e-6
+    # restart histories agree while rounding has not diverged
+    h = dict(ref.history)
+    for it, rel in info["history"][:3]:
+        if it in h and h[it] > 1e-8:
+            assert abs(rel - h[it]) <= 1e-6 * h[it]
+
+
+def test_nonsymmetric_and_resume(rbo):
+    import torch
+    A = synth.random_csr(5000, 7, seed=11)
+    b = np.random.default_rng(3).standard_normal(A.n)
+    Ad = rbo.DeviceCSR.from_host(A)
+    bd = torch.from_numpy(b).cuda()
+    x1, i1 = rbo.sstep_gmres(Ad, bd, s=5, m=20, tol=1e-4)
+    assert i1["converged"] == 1
+    x2, i2 = rbo.sstep_gmres(Ad, bd, x1.clone(), s=5, m=20, tol=1e-11)
+    assert i2["converged"] == 1 and i2["history"][0][1] <= 1e-4
+    ref = krylov.sstep_gmres(A, b, s=5, m=20, tol=1e-11)
+    xr = x2.cpu().numpy()
+    assert np.linalg.norm(b - A.to_scipy() @ xr) / np.linalg.norm(b) <= 1e-11
+    assert np.abs(xr - ref.x).max() <= 1e-8 * np.abs(ref.x).max()
+
+
+def test_not_converged_status(rbo):
+    import torch
+    A = synth.poisson3d_csr(16)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    x, info = rbo.sstep_gmres(Ad, torch.from_numpy(b).cuda(), s=5, m=10, tol=1e-12, max_restarts=2)
+    assert info["status"] == rbo.ERR_NOT_CONVERGED and info["converged"] == 0
+    assert info["restarts"] == 2
+
+
+def test_zero_rhs(rbo):
+    import torch
+    A = synth.poisson3d_csr(8)
+    Ad = rbo.DeviceCSR.from_host(A)
+    x, info = rbo.sstep_gmres(Ad, torch.zeros(A.n, dtype=torch.float64, device="cuda"), s=5, m=10)
+    assert info["converged"] == 1 and float(x.abs().max()) == 0.0

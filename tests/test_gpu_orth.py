@@ -1,0 +1,144 @@
+"""GPU parity of the block orthogonalization schemes against the oracle.
+
+Tolerances (float64 path): ||I - Q^T Q||_2 <= 1e-13, ||V - QR||_2/||V||_2 <= 1e-14,
+R within 1e-12 (normwise relative) of the oracle when every block has kappa <= 1e4.
+For ill-conditioned blocks the computed Q and R depend on rounding at the level
+eps * kappa, so parity there is checked through the two error measures, the
+per-block conditioning carried by R, and the breakdown reports."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import metrics, orth
+from oracle.sketch import Sketch as OSketch
+
+pytestmark = pytest.mark.gpu
+
+
+def run(rbo, scheme, V, s, s_hat=None, v0=False, precision=0, d=None):
+    from gpu_util import to_dev, to_host
+    n, c = V.shape
+    d = d or 4 * (c + 1 - (1 if v0 else 0) + (1 if v0 else 0))
+    sk = rbo.sketch_create(n, d, 8, 42)
+    Vd = to_dev(V)
+    if scheme == "one":
+        out = rbo.block_orth_one_stage(sk, Vd, s, v0=v0, precision=precision, raise_on_error=False)
+    elif scheme == "two":
+        out = rbo.block_orth_two_stage(sk, Vd, s, s_hat, v0=v0, precision=precision,
+                                       raise_on_error=False)
+    else:
+        out = rbo.block_orth_cholqr2(Vd, s, v0=v0, raise_on_error=False)
+    return to_host(Vd), out
+
+
+def oracle(scheme, V, s, s_hat=None, v0=False, d=None):
+    n, c = V.shape
+    d = d or 4 * (c + 1 - (1 if v0 else 0) + (1 if v0 else 0))
+    sk = OSketch(n, d, 8, 42)
+    if scheme == "one":
+        return orth.block_orth_one_stage(V, s, sk, v0=v0)
+    if scheme == "two":
+        return orth.block_orth_two_stage(V, s, s_hat, sk, v0=v0)
+    return orth.block_orth_cholqr2(V, s, v0=v0)
+
+
+@pytest.mark.parametrize("scheme,s_hat", [("one", None), ("two", 30), ("two", 10), ("cholqr2", None)])
+@pytest.mark.parametrize("n", [20000, 12347, 1001])
+def test_well_conditioned_elementwise(rbo, scheme, s_hat, n):
+    V = synth.glued_blocks(n, 12, 5, 1e4, seed=n, v0=True)
+    Q, out = run(rbo, scheme, V, 5, s_hat, v0=True)
+    ref = oracle(scheme, V, 5, s_hat, v0=True)
+    assert out.info["status"] == 0 and ref.ok
+    assert metrics.rel_diff(out.R, ref.R) <= 1e-12
+    assert np.abs(Q - ref.Q).max() <= 1e-9
+    assert metrics.orth_error(Q) <= 1e-13
+    assert metrics.backward_error(V, Q, out.R) <= 1e-14
+    assert np.allclose(np.tril(out.R, -1), 0.0) and (np.diag(out.R) > 0).all()
+
+
+@pytest.mark.parametrize("scheme,s_hat", [("one", None), ("two", 30), ("two", 60)])
+def test_config0_kappa_1e10(rbo, scheme, s_hat):
+    # 20000 x 60, 12 blocks of 5 with kappa = 1e10 each, sparse-sign d = 4*61, zeta 8, seed 42
+    V = synth.glued_blocks(20000, 12, 5, 1e10, seed=0)
+    Q, out = run(rbo, scheme, V, 5, s_hat, d=244)
+    assert out.info["status"] == 0
+    assert metrics.orth_error(Q) <= 1e-13
+    assert metrics.backward_error(V, Q, out.R) <= 1e-14
+    ref = oracle(scheme, V, 5, s_hat, d=244)
+    for j in range(12):
+        c_gpu = metrics.cond2(out.R[5 * j:5 * j + 5, 5 * j:5 * j + 5])
+        c_ref = metrics.cond2(ref.R[5 * j:5 * j + 5, 5 * j:5 * j + 5])
+        assert abs(np.log10(c_gpu) - np.log10(c_ref)) < 0.01
+    # R is unique: agreement is limited by conditioning (eps * kappa)
+    assert metrics.rel_diff(out.R, ref.R) <= 1e-4
+
+
+def test_cholqr2_breakdown_reported(rbo):
+    V = synth.glued_blocks(20000, 12, 5, 1e10, seed=0)
+    Q, out = run(rbo, "cholqr2", V, 5)
+    ref = oracle("cholqr2", V, 5)
+    assert not ref.ok
+    assert out.info["status"] == rbo.ERR_CHOL_BREAKDOWN
+    assert out.info["breakdown_block"] == 0
+    assert out.info["breakdown_stage_name"] in ("intra", "intra2", "final")
+    assert 0 <= out.info["breakdown_column"] < 5
+
+
+@pytest.mark.parametrize("kappa", [1e4, 1e8, 1e12, 1e14])
+def test_two_stage_kappa_sweep(rbo, kappa):
+    V = synth.glued_blocks(30000, 12, 5, kappa, seed=17, v0=True)
+    Q, out = run(rbo, "two", V, 5, 30, v0=True)
+    assert out.info["status"] == 0
+    assert metrics.orth_error(Q) <= 1e-13
+    assert metrics.backward_error(V, Q, out.R) <= 1e-14
+
+
+@pytest.mark.parametrize("scheme", ["one", "two"])
+def test_mixed_precision_meets_fp64_bounds_at_moderate_kappa(rbo, scheme):
+    V = synth.glued_blocks(20000, 12, 5, 1e4, seed=9, v0=True)
+    Q, out = run(rbo, scheme, V, 5, 30, v0=True, precision=rbo.PREC_MIXED)
+    ref = oracle(scheme, V, 5, 30, v0=True)
+    assert out.info["status"] == 0
+    assert metrics.orth_error(Q) <= 1e-13
+    assert metrics.backward_error(V, Q, out.R) <= 1e-14
+    assert metrics.rel_diff(out.R, ref.R) <= 1e-12
+
+
+@pytest.mark.parametrize("n,s,nb", [(7, 1, 5), (64, 5, 2), (65, 5, 2), (129, 16, 8), (3, 3, 1)])
+def test_edge_shapes(rbo, n, s, nb):
+    V = synth.glued_blocks(n, nb, s, 10.0, seed=n)
+    Q, out = run(rbo, "one", V, s, d=max(4 * (nb * s + 1), 16))
+    ref = oracle("one", V, s, d=max(4 * (nb * s + 1), 16))
+    assert out.info["status"] == 0
+    assert metrics.rel_diff(out.R, ref.R) <= 1e-12
+    assert metrics.orth_error(Q) <= 1e-13
+
+
+def test_invalid_arguments_are_rejected(rbo):
+    import torch
+    from gpu_util import to_dev
+    V = to_dev(np.random.default_rng(0).standard_normal((100, 12)))
+    sk = rbo.sketch_create(100, 52, 8, 42)
+    with pytest.raises(rbo.RboError) as e:
+        rbo.block_orth_one_stage(sk, V, 5)  # 12 not a multiple of 5
+    assert e.value.code == rbo.ERR_ARG
+    with pytest.raises(rbo.RboError):
+        rbo.block_orth_two_stage(sk, V, 4, 6)  # s does not divide s_hat
+    small = rbo.sketch_create(10, 52, 8, 42)
+    with pytest.raises(rbo.RboError):
+        rbo.block_orth_one_stage(small, V, 4)  # sketch too short for n
+
+
+def test_rank_deficient_block_reports_breakdown(rbo):
+    V = synth.glued_blocks(5000, 3, 5, 1e4, seed=1)
+    V[:, 7] = V[:, 6]  # exact duplicate column inside block 1
+    Q, out = run(rbo, "one", V, 5, d=64)
+    assert out.info["status"] == rbo.ERR_CHOL_BREAKDOWN
+    assert out.info["breakdown_block"] == 1
+
+
+def test_nan_input_reports_breakdown_not_silence(rbo):
+    V = synth.glued_blocks(5000, 2, 5, 1e2, seed=2)
+    V[10, 3] = np.nan
+    Q, out = run(rbo, "one", V, 5, d=64)
+    assert out.info["status"] == rbo.ERR_CHOL_BREAKDOWN
