@@ -160,32 +160,13 @@ def run_ours(args):
     sec_per_solve = ms_per_step / 2.0 / 1e3
 
     # per-kernel times with CUDA events around each library launch (same steps again)
-    rbo.profile_reset()
-    rbo.profile_enable(True)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        step()
-    e1.record()
-    barrier()
-    ms_prof = e0.elapsed_time(e1) / args.steps
-    prof = {k: rbo.profile_read(v) for k, v in
-            (("rowpass", rbo.PROF_ROWPASS), ("spmv", rbo.PROF_SPMV), ("vector", rbo.PROF_VECTOR))}
-    rbo.profile_enable(False)
-    rp = prof["rowpass"]
-    avg_ms = rp["ms"] / max(rp["launches"], 1)
-    achieved_flops = rp["flops"] / (rp["ms"] / 1e3) if rp["ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "rowpass_kernel<false> (fused FP64 row pass)",
-                "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_DERIVED / 1e12,
-                "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_DERIVED,
-                "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 1.25 TFLOP/s nominal)",
-                "traffic": None, "launches": rp["launches"], "avg_launch_us": avg_ms * 1e3,
-                "hbm_gbs_algorithmic": rp["bytes"] / (rp["ms"] / 1e3) / 1e9 if rp["ms"] > 0 else 0.0,
-                "share_of_step": rp["ms"] / args.steps / ms_prof if ms_prof > 0 else None}
+    if args.no_prof:
+        prof, roofline, ms_prof = None, None, None
+    else:
+        prof, roofline, ms_prof = profile_steps(rbo, torch, step, barrier, args)
 
     # end-to-end through the public API with host buffers
-    e2e = run_e2e(rbo, torch, A, b_host, args)
+    e2e = None if args.no_e2e else run_e2e(rbo, torch, A, b_host, args)
 
     orth = run_orth(rbo, torch, args) if (rank == 0 and not args.no_orth) else None
     cpu = None
@@ -220,6 +201,35 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def profile_steps(rbo, torch, step, barrier, args):
+    rbo.profile_reset()
+    rbo.profile_enable(True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    barrier()
+    ms_prof = e0.elapsed_time(e1) / args.steps
+    prof = {k: rbo.profile_read(v) for k, v in
+            (("rowpass", rbo.PROF_ROWPASS), ("spmv", rbo.PROF_SPMV), ("vector", rbo.PROF_VECTOR))}
+    rbo.profile_enable(False)
+    rp = prof["rowpass"]
+    avg_ms = rp["ms"] / max(rp["launches"], 1)
+    achieved_flops = rp["flops"] / (rp["ms"] / 1e3) if rp["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "rowpass_kernel<false> (fused FP64 row pass)",
+                "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_DERIVED / 1e12,
+                "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_DERIVED,
+                "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 1.25 TFLOP/s nominal)",
+                "traffic": None, "launches": rp["launches"], "avg_launch_us": avg_ms * 1e3,
+                "hbm_gbs_algorithmic": rp["bytes"] / (rp["ms"] / 1e3) / 1e9 if rp["ms"] > 0 else 0.0,
+                "share_of_step": rp["ms"] / args.steps / ms_prof if ms_prof > 0 else None}
+
+    return prof, roofline, ms_prof
+
 
 
 def run_e2e(rbo, torch, A, b_host, args):
@@ -388,6 +398,8 @@ def main():
     ap.add_argument("--no-orth", action="store_true")
     ap.add_argument("--quick-orth", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-prof", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -1,0 +1,62 @@
+"""Block orthogonalization at the full 2^24 x 61 size (v0 + 12 glued blocks of 5,
+two-stage s_hat = 30 and one-stage, the launch configuration the bench times).
+The oracle cannot run at this size in seconds, so parity is checked through
+properties that hold at any size: ||I - Q^T Q||_2 <= 1e-13, ||V - QR||_2/||V||_2 <=
+1e-14 (both evaluated with cuBLAS float64 GEMMs, independent of the library's
+kernels), R upper triangular with positive diagonal, the per-block condition
+numbers carried by R's diagonal blocks (the glued construction fixes them), and
+R on sampled rows: the oracle's float64 product Q[r, :] R must reproduce V[r, :]."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import metrics
+
+pytestmark = pytest.mark.gpu
+
+N = 1 << 24
+
+
+def _check(rbo, torch, V0, scheme, precision, kappa):
+    c = V0.shape[0]
+    W = V0.clone()
+    Wm = W.t()
+    sk = rbo.sketch_create(N, 4 * c, 8, 42)
+    if scheme == "two":
+        out = rbo.block_orth_two_stage(sk, Wm, 5, 30, v0=True, precision=precision)
+    else:
+        out = rbo.block_orth_one_stage(sk, Wm, 5, v0=True, precision=precision)
+    R = out.R
+    assert np.allclose(np.tril(R, -1), 0.0) and (np.diag(R) > 0).all()
+    G = (W @ W.t()).cpu().numpy()                      # Q^T Q, cuBLAS
+    oe = float(np.max(np.abs(np.linalg.eigvalsh(np.eye(c) - 0.5 * (G + G.T)))))
+    assert oe <= 1e-13, oe
+    Rt = torch.from_numpy(R).cuda()
+    D = V0.t() - Wm @ Rt                               # V - Q R, cuBLAS
+    nD = float(torch.linalg.matrix_norm(D, ord=2))
+    nV = float(torch.linalg.matrix_norm(V0.t(), ord=2))
+    assert nD / nV <= 1e-14, nD / nV
+    # sampled rows with the oracle's arithmetic (extended precision products)
+    rows = np.random.default_rng(0).choice(N, 256, replace=False)
+    Qs = Wm[rows].cpu().numpy()
+    Vs = V0.t()[rows].cpu().numpy()
+    bwd = np.abs((Qs.astype(np.longdouble) @ R.astype(np.longdouble)) - Vs).max()
+    assert bwd <= 1e-14 * nV
+    for j in range(12):
+        cj = metrics.cond2(R[1 + 5 * j:6 + 5 * j, 1 + 5 * j:6 + 5 * j])
+        assert abs(np.log10(cj) - np.log10(kappa)) < 0.05
+    return out
+
+
+@pytest.mark.parametrize("scheme", ["two", "one"])
+@pytest.mark.parametrize("kappa", [1e8, 1e14])
+def test_full_size_fp64(rbo, scheme, kappa):
+    import torch
+    V0 = synth.glued_blocks_torch(N, 12, 5, kappa, seed=1, v0=True, device="cuda")
+    _check(rbo, torch, V0, scheme, rbo.PREC_FP64, kappa)
+
+
+def test_full_size_mixed_at_kappa_1e4(rbo):
+    import torch
+    V0 = synth.glued_blocks_torch(N, 12, 5, 1e4, seed=2, v0=True, device="cuda")
+    _check(rbo, torch, V0, "two", rbo.PREC_MIXED, 1e4)
