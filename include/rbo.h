@@ -45,6 +45,11 @@ extern "C" {
 #define RBO_ERR_SKETCH         -6  /* a sketch column found < zeta distinct rows         */
 #define RBO_ERR_NOMEM          -7  /* workspace allocation failed                        */
 #define RBO_ERR_NO_DEVICE      -8  /* no CUDA device / not an sm_103 device              */
+#define RBO_ERR_LOST_ORTHOGONALITY -9  /* the final CholQR of a block met a Gram far from I:
+                                      the first intra-block step failed at the working
+                                      precision (block numerically rank deficient, or
+                                      beyond the mixed-precision range); info->
+                                      breakdown_block says which block                   */
 
 /* ---- precision modes --------------------------------------------------------- */
 #define RBO_PREC_FP64   0  /* every step in IEEE float64 (the reference path)          */
@@ -186,6 +191,50 @@ int rbo_mpk_csr(const rbo_csr* A, const double* dscale, int32_t s, const double*
 int rbo_sstep_gmres(const rbo_csr* A, const double* b, double* x, int32_t s, int32_t s_hat,
                     int32_t m, double tol, rbo_sketch sk, const rbo_opts* opts, rbo_info* info,
                     void* stream);
+
+/* s-step GMRES with a caller-supplied right preconditioner M that has A's sparsity
+ * pattern: Mval (device, A->nnz values in A's CSR order).  The matrix-powers kernel
+ * applies A M (two SpMVs per basis vector; the operator stays linear, so s-step
+ * GMRES stays valid, Section 4) and the solution update is x += M Q z.  Other
+ * arguments, errors and convergence test as rbo_sstep_gmres; opts->precond is
+ * ignored.  Used with the learned preconditioner below.                            */
+int rbo_sstep_gmres_precond(const rbo_csr* A, const double* Mval, const double* b, double* x,
+                            int32_t s, int32_t s_hat, int32_t m, double tol, rbo_sketch sk,
+                            const rbo_opts* opts, rbo_info* info, void* stream);
+
+/* ---- learned sparse-approximate-inverse preconditioner -----------------------------
+ * Not in the paper: a graph network (3 message-passing layers, width 32, BF16
+ * weights, FP32 activations and accumulation) maps the entries of A to the values
+ * of a right preconditioner M on A's pattern, keeping the matrix-powers kernel
+ * linear.  Nodes are rows of A, each stored entry (i, j) an edge from j to i; with
+ * D = diag(A) and Ahat = D^-1 A the inputs are, per node, the off-diagonal row and
+ * column sums of |Ahat| and, per edge, (Ahat_ij, Ahat_ji, [i == j]); the output is
+ * M_ij = (network output + [i == j]) / A_ii, so an untrained network (zero output
+ * layer) is the Jacobi preconditioner.  Training minimises
+ * mean_k ||r_k - A M r_k||^2 / ||r_k||^2 over residual vectors r_k (Adam, FP32 master
+ * weights).  A must be square with a nonzero diagonal and a structurally symmetric
+ * pattern (RBO_ERR_ARG otherwise).  The handle owns ~0.3 MB of device memory;
+ * calls use the per-device workspace arena.  Parameters are a flat float vector of
+ * rbo_gnn_param_count() values in the order Wn(32x2) bn We(32x3) be, then per layer
+ * Wm(32x64) bm Wh(32x64) bh, then wo(96) bo (row-major matrices).              */
+typedef struct rbo_gnn_s* rbo_gnn;
+int rbo_gnn_param_count(void);
+/* Random He-scaled hidden weights from `seed`, zero biases and output layer.       */
+int rbo_gnn_create(uint64_t seed, rbo_gnn* out);
+int rbo_gnn_destroy(rbo_gnn g);
+/* FP32 master weights from / to host memory (set also resets the Adam state).      */
+int rbo_gnn_set_params(rbo_gnn g, const float* host);
+int rbo_gnn_get_params(rbo_gnn g, float* host);
+/* Mval (device, A->nnz) = M on A's pattern for the current weights.                */
+int rbo_gnn_infer(rbo_gnn g, const rbo_csr* A, double* Mval, void* stream);
+/* Loss over the nr residual columns of R (device, n x nr, ld ldr >= n, nr <= 64)
+ * and its gradient with respect to the parameters (grad_host may be NULL).          */
+int rbo_gnn_loss_grad(rbo_gnn g, const rbo_csr* A, const double* R, int32_t nr, int64_t ldr,
+                      double* loss, float* grad_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on that loss;
+ * *loss receives the loss before the step.                                        */
+int rbo_gnn_train_step(rbo_gnn g, const rbo_csr* A, const double* R, int32_t nr, int64_t ldr,
+                       float lr, double* loss, void* stream);
 
 /* ---- per-kernel timing ---------------------------------------------------------------
  * When enabled, every kernel the library enqueues is bracketed by two CUDA events on

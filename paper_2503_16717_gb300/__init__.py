@@ -40,6 +40,7 @@ ERR_TIMEOUT = -5
 ERR_SKETCH = -6
 ERR_NOMEM = -7
 ERR_NO_DEVICE = -8
+ERR_LOST_ORTHOGONALITY = -9
 PREC_FP64 = 0
 PREC_MIXED = 1
 INTRA_RANDCHOLQR = 0

@@ -105,7 +105,7 @@ int finish_status(Arena* ar, cudaStream_t st, rbo_info* info) {
     info->breakdown_block = -1;
     info->breakdown_column = -1;
     info->breakdown_stage = 0;
-    if (s.code == RBO_ERR_CHOL_BREAKDOWN) {
+    if (s.code == RBO_ERR_CHOL_BREAKDOWN || s.code == RBO_ERR_LOST_ORTHOGONALITY) {
       info->breakdown_block = s.block;
       info->breakdown_column = s.column;
       info->breakdown_stage = s.stage;
@@ -172,6 +172,7 @@ const char* rbo_status_string(int s) {
     case RBO_ERR_SKETCH: return "sketch column without zeta distinct rows";
     case RBO_ERR_NOMEM: return "workspace allocation failed";
     case RBO_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    case RBO_ERR_LOST_ORTHOGONALITY: return "loss of orthogonality in a block (first intra step failed)";
     default: return "unknown status";
   }
 }

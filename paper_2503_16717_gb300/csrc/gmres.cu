@@ -53,20 +53,22 @@ struct GmresWork {
   int64_t ldq;
   double* vals;     // scaled CSR values (Jacobi)
   double* dscale;   // 1 / diag(A)
-  double* y;        // right-preconditioned iterate
+  double* t1;       // temporaries (n)
+  double* t2;
   double* zdev;     // m
   double* Rdev;     // (m+1) x (m+1)
   double* coords;   // (m+1) x s_hat
   double* bn;       // 1 (||b||^2)
 };
 
-int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_hat, int m,
-                     double tol, int d, int zeta, uint64_t seed, const rbo_opts* opts,
-                     rbo_info* info, cudaStream_t st, int* launches_out) {
+int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, double* x, int s,
+                     int s_hat, int m, double tol, int d, int zeta, uint64_t seed,
+                     const rbo_opts* opts, rbo_info* info, cudaStream_t st, int* launches_out) {
   const int64_t n = A->n;
   const bool two = s_hat > s;
   const int K = two ? s_hat : s;
-  const int precond = opts ? opts->precond : 1;
+  // 0: none, 1: Jacobi (scaled copy of the values), 2: M on A's pattern (Mval)
+  const int precond = Mval ? 2 : (opts ? (opts->precond ? 1 : 0) : 1);
   const int max_restarts = (opts && opts->max_restarts > 0) ? opts->max_restarts : 1000;
   const int ld = m + 1;
   const int64_t ldq = (n + 1) & ~int64_t(1);  // even: 16-byte aligned columns
@@ -83,14 +85,16 @@ int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_
   GmresWork w;
   w.ldq = ldq;
   w.Qb = (double*)ar->take((size_t)ldq * (m + 1) * 8);
-  w.vals = precond ? (double*)ar->take((size_t)std::max<int64_t>(A->nnz, 1) * 8) : nullptr;
-  w.dscale = precond ? (double*)ar->take((size_t)n * 8) : nullptr;
-  w.y = (double*)ar->take((size_t)n * 8);
+  w.vals = precond == 1 ? (double*)ar->take((size_t)std::max<int64_t>(A->nnz, 1) * 8) : nullptr;
+  w.dscale = precond == 1 ? (double*)ar->take((size_t)n * 8) : nullptr;
+  w.t1 = (double*)ar->take((size_t)n * 8);
+  w.t2 = (double*)ar->take((size_t)n * 8);
   w.zdev = (double*)ar->take((size_t)m * 8 + 64);
   w.Rdev = (double*)ar->take((size_t)ld * ld * 8);
   w.coords = (double*)ar->take((size_t)ld * K * 8);
   w.bn = (double*)ar->take(64);
-  if (!w.Qb || !w.y || !w.zdev || !w.Rdev || !w.coords || !w.bn || (precond && (!w.vals || !w.dscale)))
+  if (!w.Qb || !w.t1 || !w.t2 || !w.zdev || !w.Rdev || !w.coords || !w.bn ||
+      (precond == 1 && (!w.vals || !w.dscale)))
     return RBO_ERR_NOMEM;
 
   OrthCtx c;
@@ -104,15 +108,26 @@ int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_
 
   CsrDev Araw{n, A->nnz, A->rowptr, A->col, A->val};
   CsrDev Ahat = Araw;
-  if (precond) {
+  CsrDev Mop{n, A->nnz, A->rowptr, A->col, Mval};
+  if (precond == 1) {
     if ((e = jacobi_launch(Araw, w.dscale, ar->status, st))) return e;
     if ((e = scale_columns_launch(Araw, w.dscale, w.vals, st))) return e;
     Ahat.val = w.vals;
     c.launches += 2;
   }
-  // y0 = D x0  (x = D^{-1} y with D^{-1} = dscale)
-  if ((e = scale_vec_launch(n, w.dscale, x, w.y, 1, st))) return e;
-  c.launches += 1;
+  // out = A M u: one SpMV with the column-scaled values (Jacobi), two SpMVs (M given),
+  // or one SpMV with A (no preconditioner)
+  auto apply_op = [&](const double* u, double* out) -> int {
+    int r;
+    if (precond == 2) {
+      if ((r = spmv_launch(Mop, nullptr, u, w.t2, ar->status, st))) return r;
+      if ((r = spmv_launch(Araw, nullptr, w.t2, out, ar->status, st))) return r;
+      c.launches += 2;
+      return RBO_OK;
+    }
+    c.launches += 1;
+    return spmv_launch(Ahat, nullptr, u, out, ar->status, st);
+  };
   // ||b||
   {
     RowPass r;
@@ -139,7 +154,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_
   int cycle = 0;
   for (cycle = 0; cycle <= max_restarts; ++cycle) {
     // r = b - Ahat y into basis column 0, q0 = r / ||r||
-    if ((e = residual_launch(Ahat, b, w.y, w.Qb, ar->status, st))) return e;
+    if ((e = residual_launch(Araw, b, x, w.Qb, ar->status, st))) return e;
     c.launches += 1;
     if (cudaMemsetAsync(w.Rdev, 0, (size_t)ld * ld * 8, st) != cudaSuccess) return RBO_ERR_CUDA;
     if ((e = normalise_column(c, n, w.Qb, w.Rdev, ld, 0))) return e;
@@ -173,12 +188,8 @@ int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_
       if (!two) {
         double* W = w.Qb + (int64_t)P * ldq;
         const double* u = w.Qb + (int64_t)(P - 1) * ldq;
-        for (int i = 0; i < s; ++i) {
-          if ((e = spmv_launch(Ahat, nullptr, i == 0 ? u : W + (int64_t)(i - 1) * ldq,
-                               W + (int64_t)i * ldq, ar->status, st)))
-            return e;
-          c.launches += 1;
-        }
+        for (int i = 0; i < s; ++i)
+          if ((e = apply_op(i == 0 ? u : W + (int64_t)(i - 1) * ldq, W + (int64_t)i * ldq))) return e;
         if ((e = one_stage_block(c, n, w.Qb, ldq, P, W, ldq, s, RBO_INTRA_RANDCHOLQR, w.Rdev, ld, P,
                                  blk)))
           return e;
@@ -209,12 +220,9 @@ int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_
             gens.push_back(bp.cols - 1);
           }
           double* W = bp.VB + (int64_t)bp.cols * ldq;
-          for (int i = 0; i < s; ++i) {
-            if ((e = spmv_launch(Ahat, nullptr, i == 0 ? u : W + (int64_t)(i - 1) * ldq,
-                                 W + (int64_t)i * ldq, ar->status, st)))
+          for (int i = 0; i < s; ++i)
+            if ((e = apply_op(i == 0 ? u : W + (int64_t)(i - 1) * ldq, W + (int64_t)i * ldq)))
               return e;
-            c.launches += 1;
-          }
           if ((e = bigpanel_add(c, bp, s))) return e;
         }
         if ((e = bigpanel_finish(c, bp, w.Rdev, ld, P, w.coords, ld))) return e;
@@ -261,11 +269,17 @@ int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_
     const int k = ncols - 1;
     if (cudaMemcpyAsync(w.zdev, z.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return RBO_ERR_CUDA;
-    if ((e = gemv_update_launch(n, k, w.Qb, ldq, w.zdev, w.y, st))) return e;
-    c.launches += 1;
+    // x += M (Q z)
+    if ((e = gemv_update_launch(n, k, w.Qb, ldq, w.zdev, w.t1, 0, st))) return e;
+    if (precond == 2) {
+      if ((e = spmv_launch(Mop, nullptr, w.t1, w.t2, ar->status, st))) return e;
+      if ((e = axpy_scaled_launch(n, nullptr, w.t2, x, st))) return e;
+      c.launches += 3;
+    } else {
+      if ((e = axpy_scaled_launch(n, w.dscale, w.t1, x, st))) return e;
+      c.launches += 2;
+    }
   }
-  if ((e = scale_vec_launch(n, w.dscale, w.y, x, 0, st))) return e;
-  c.launches += 1;
   if (cudaStreamSynchronize(st) != cudaSuccess) return RBO_ERR_CUDA;
   if (info) {
     info->iterations = its;
@@ -281,9 +295,9 @@ int sstep_gmres_impl(const rbo_csr* A, const double* b, double* x, int s, int s_
 }  // namespace rbo
 
 
-extern "C" int rbo_sstep_gmres(const rbo_csr* A, const double* b, double* x, int32_t s,
-                               int32_t s_hat, int32_t m, double tol, rbo_sketch sk,
-                               const rbo_opts* opts, rbo_info* info, void* stream) {
+static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double* b, double* x,
+                             int32_t s, int32_t s_hat, int32_t m, double tol, rbo_sketch sk,
+                             const rbo_opts* opts, rbo_info* info, void* stream) {
   using namespace rbo;
   auto t0 = std::chrono::steady_clock::now();
   if (info) {
@@ -324,7 +338,7 @@ extern "C" int rbo_sstep_gmres(const rbo_csr* A, const double* b, double* x, int
     if (major != 10 || minor != 3) code = RBO_ERR_NO_DEVICE;
   }
   if (code == RBO_OK)
-    code = sstep_gmres_impl(A, b, x, s, s_hat, m, tol, d, zeta, seed, opts, info,
+    code = sstep_gmres_impl(A, Mval, b, x, s, s_hat, m, tol, d, zeta, seed, opts, info,
                             (cudaStream_t)stream, &launches);
   if (info) {
     info->status = code;
@@ -333,4 +347,18 @@ extern "C" int rbo_sstep_gmres(const rbo_csr* A, const double* b, double* x, int
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return code;
+}
+
+extern "C" int rbo_sstep_gmres(const rbo_csr* A, const double* b, double* x, int32_t s,
+                               int32_t s_hat, int32_t m, double tol, rbo_sketch sk,
+                               const rbo_opts* opts, rbo_info* info, void* stream) {
+  return sstep_gmres_entry(A, nullptr, b, x, s, s_hat, m, tol, sk, opts, info, stream);
+}
+
+extern "C" int rbo_sstep_gmres_precond(const rbo_csr* A, const double* Mval, const double* b,
+                                       double* x, int32_t s, int32_t s_hat, int32_t m, double tol,
+                                       rbo_sketch sk, const rbo_opts* opts, rbo_info* info,
+                                       void* stream) {
+  if (!Mval) return RBO_ERR_ARG;
+  return sstep_gmres_entry(A, Mval, b, x, s, s_hat, m, tol, sk, opts, info, stream);
 }

@@ -1,0 +1,497 @@
+// Learned sparse-approximate-inverse preconditioner: a 3-layer message-passing
+// network (width 32, BF16 weights, FP32 activations and accumulation) that maps the
+// entries of A to the values of a right preconditioner M on A's own pattern, with
+// hand-written forward, backward and Adam kernels.
+//
+// Graph: nodes = rows of A; every stored entry (i, j) is an edge carrying a message
+// from node j to node i.  Ahat = D^{-1} A.
+//   f_i  = [sum_{j!=i} |Ahat_ij|, sum_{j!=i} |Ahat_ji|]
+//   x_ij = [Ahat_ij, Ahat_ji, [i == j]]
+//   h0 = relu(Wn f + bn), e0 = relu(We x + be)
+//   layer: m_ij = relu(Wm [e_ij; h_j] + bm); agg_i = sum_j m_ij;
+//          h_i += relu(Wh [h_i; agg_i] + bh); e_ij += m_ij
+//   M_ij = (wo . [e_ij; h_i; h_j] + bo + [i == j]) / A_ii
+// Loss over residual columns r_k: mean_k ||r_k - A M r_k||^2 / ||r_k||^2.
+//
+// One warp handles one node or edge with lane = channel (width 32 = warp size);
+// matrix-vector products broadcast the input channels with shuffles.  Every sum
+// over edges or nodes runs in a fixed order (rows in CSR order, per-block partials
+// reduced in block order), so results are reproducible.  The pattern of A must be
+// structurally symmetric (the transpose of edge (i, j) is located by binary search
+// in row j); stencil matrices are.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace rbo {
+namespace gnn {
+
+constexpr int W = 32;
+constexpr int NL = 3;
+constexpr int OFF_WN = 0, OFF_BN = 64, OFF_WE = 96, OFF_BE = 192, OFF_L0 = 224;
+constexpr int LAYER_SZ = 2048 + 32 + 2048 + 32;
+constexpr int OFF_WO = OFF_L0 + NL * LAYER_SZ;  // 12704
+constexpr int OFF_BO = OFF_WO + 96;
+constexpr int NPARAM = OFF_BO + 1;               // 12801
+__host__ __device__ constexpr int off_wm(int l) { return OFF_L0 + l * LAYER_SZ; }
+__host__ __device__ constexpr int off_bm(int l) { return off_wm(l) + 2048; }
+__host__ __device__ constexpr int off_wh(int l) { return off_wm(l) + 2080; }
+__host__ __device__ constexpr int off_bh(int l) { return off_wm(l) + 4128; }
+
+__device__ __forceinline__ float bf(const __nv_bfloat16* w, int i) { return __bfloat162float(w[i]); }
+__device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
+
+// ---- graph construction ---------------------------------------------------------------
+// per row: row id of every edge, diagonal value, position of (j, i) for every (i, j)
+__global__ void graph_edges_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ col, const double* __restrict__ val,
+                                   int32_t* __restrict__ erow, int32_t* __restrict__ tpos,
+                                   double* __restrict__ dinv, DevStatus* status) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int beg = rowptr[i], end = rowptr[i + 1];
+  double dia = 0.0;
+  for (int e = beg; e < end; ++e) {
+    erow[e] = (int32_t)i;
+    const int j = col[e];
+    if (j == (int)i) dia = val[e];
+    // binary search for column i in row j (columns sorted)
+    int lo = rowptr[j], hi = rowptr[j + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int cm = col[mid];
+      if (cm == (int)i) { pos = mid; break; }
+      if (cm < (int)i) lo = mid + 1; else hi = mid - 1;
+    }
+    tpos[e] = pos;
+    if (pos < 0) set_error(status, RBO_ERR_ARG, 20);
+  }
+  if (dia == 0.0) set_error(status, RBO_ERR_ARG, 21);
+  dinv[i] = dia != 0.0 ? 1.0 / dia : 0.0;
+}
+
+__global__ void graph_features_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ col, const double* __restrict__ val,
+                                      const int32_t* __restrict__ tpos, const double* __restrict__ dinv,
+                                      float* __restrict__ x, float* __restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double rs = 0.0, cs = 0.0;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int j = col[e];
+    const double ah = val[e] * dinv[i];
+    const double aht = tpos[e] >= 0 ? val[tpos[e]] * dinv[j] : 0.0;
+    x[3 * (int64_t)e + 0] = (float)ah;
+    x[3 * (int64_t)e + 1] = (float)aht;
+    x[3 * (int64_t)e + 2] = (j == (int)i) ? 1.f : 0.f;
+    if (j != (int)i) {
+      rs += fabs(ah);
+      cs += fabs(aht);
+    }
+  }
+  f[2 * i] = (float)rs;
+  f[2 * i + 1] = (float)cs;
+}
+
+// ---- forward ------------------------------------------------------------------------
+// h[i][c] = relu(Wn[c] . f_i + bn[c])  and  e[e][c] = relu(We[c] . x_e + be[c])
+__global__ void encode_kernel(int64_t cnt, int nin, const float* __restrict__ in,
+                              const __nv_bfloat16* __restrict__ w, int off_w, int off_b,
+                              float* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= cnt * W) return;
+  const int64_t it = t / W;
+  const int c = (int)(t % W);
+  float z = bf(w, off_b + c);
+  for (int k = 0; k < nin; ++k) z = fmaf(bf(w, off_w + c * nin + k), in[it * nin + k], z);
+  out[t] = relu(z);
+}
+
+// message layer: warp per edge, lane = output channel
+__global__ void message_kernel(int64_t nnz, const int32_t* __restrict__ col,
+                               const float* __restrict__ ein, const float* __restrict__ h,
+                               const __nv_bfloat16* __restrict__ w, int l, float* __restrict__ m,
+                               float* __restrict__ eout) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float wr[2 * W];
+#pragma unroll
+  for (int k = 0; k < 2 * W; ++k) wr[k] = bf(w, off_wm(l) + lane * 2 * W + k);
+  const float bias = bf(w, off_bm(l) + lane);
+  for (int64_t e = warp0; e < nnz; e += nwarps) {
+    const float ev = ein[e * W + lane];
+    const float hv = h[(int64_t)col[e] * W + lane];
+    float z = bias;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      z = fmaf(wr[k], __shfl_sync(0xffffffffu, ev, k), z);
+      z = fmaf(wr[W + k], __shfl_sync(0xffffffffu, hv, k), z);
+    }
+    const float mv = relu(z);
+    m[e * W + lane] = mv;
+    eout[e * W + lane] = ev + mv;
+  }
+}
+
+// aggregation + node update: warp per node
+__global__ void node_update_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                   const float* __restrict__ m, const float* __restrict__ hin,
+                                   const __nv_bfloat16* __restrict__ w, int l,
+                                   float* __restrict__ agg, float* __restrict__ rh,
+                                   float* __restrict__ hout) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float wr[2 * W];
+#pragma unroll
+  for (int k = 0; k < 2 * W; ++k) wr[k] = bf(w, off_wh(l) + lane * 2 * W + k);
+  const float bias = bf(w, off_bh(l) + lane);
+  for (int64_t i = warp0; i < n; i += nwarps) {
+    float a = 0.f;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) a += m[(int64_t)e * W + lane];
+    const float hv = hin[i * W + lane];
+    float z = bias;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      z = fmaf(wr[k], __shfl_sync(0xffffffffu, hv, k), z);
+      z = fmaf(wr[W + k], __shfl_sync(0xffffffffu, a, k), z);
+    }
+    const float r = relu(z);
+    agg[i * W + lane] = a;
+    rh[i * W + lane] = r;
+    hout[i * W + lane] = hv + r;
+  }
+}
+
+// decoder: M_e = (wo . [e; h_i; h_j] + bo + [i == j]) / A_ii, warp per edge
+__global__ void decode_kernel(int64_t nnz, const int32_t* __restrict__ erow,
+                              const int32_t* __restrict__ col, const float* __restrict__ e,
+                              const float* __restrict__ h, const __nv_bfloat16* __restrict__ w,
+                              const double* __restrict__ dinv, double* __restrict__ Mval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float w0 = bf(w, OFF_WO + lane), w1 = bf(w, OFF_WO + W + lane), w2 = bf(w, OFF_WO + 2 * W + lane);
+  const float bo = bf(w, OFF_BO);
+  for (int64_t q = warp0; q < nnz; q += nwarps) {
+    const int i = erow[q], j = col[q];
+    float s = w0 * e[q * W + lane] + w1 * h[(int64_t)i * W + lane] + w2 * h[(int64_t)j * W + lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const float out = s + bo + (i == j ? 1.f : 0.f);
+      Mval[q] = (double)out * dinv[i];
+    }
+  }
+}
+
+// ---- loss (float64) ---------------------------------------------------------------------
+// Z = Mat R  for a matrix with A's pattern and values `v` (R: n x nr, ld ldr)
+__global__ void spmm_kernel(int64_t n, int nr, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ col, const double* __restrict__ v,
+                            const double* __restrict__ R, int64_t ldr, double* __restrict__ Z,
+                            int64_t ldz) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nr) return;
+  const int64_t i = t % n;
+  const int k = (int)(t / n);
+  double s = 0.0;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) s = fma(v[e], R[col[e] + k * ldr], s);
+  Z[i + k * ldz] = s;
+}
+
+// (A^T Y)_i = sum over stored (j, i) of A_ji Y_j = sum over row i of A[tpos] Y[col]
+__global__ void spmm_t_kernel(int64_t n, int nr, const int32_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ col, const int32_t* __restrict__ tpos,
+                              const double* __restrict__ v, const double* __restrict__ Y,
+                              int64_t ldy, double* __restrict__ Z, int64_t ldz) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nr) return;
+  const int64_t i = t % n;
+  const int k = (int)(t / n);
+  double s = 0.0;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) s = fma(v[tpos[e]], Y[col[e] + k * ldy], s);
+  Z[i + k * ldz] = s;
+}
+
+// per-block partial sums of ||R_k - Y_k||^2 and ||R_k||^2 ; E = R - Y written to Y
+__global__ void residual_norms_kernel(int64_t n, int nr, const double* __restrict__ R, int64_t ldr,
+                                      double* __restrict__ Y, int64_t ldy, double* __restrict__ part) {
+  __shared__ double red[2][256];
+  const int k = blockIdx.y;
+  double se = 0.0, sr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = R[i + k * ldr];
+    const double e = r - Y[i + k * ldy];
+    Y[i + k * ldy] = e;
+    se = fma(e, e, se);
+    sr = fma(r, r, sr);
+  }
+  red[0][threadIdx.x] = se;
+  red[1][threadIdx.x] = sr;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * ((int64_t)k * gridDim.x + blockIdx.x)] = red[0][0];
+    part[2 * ((int64_t)k * gridDim.x + blockIdx.x) + 1] = red[1][0];
+  }
+}
+
+__global__ void scale_cols_kernel(int64_t n, int nr, double* __restrict__ Y, int64_t ldy,
+                                  const double* __restrict__ colscale) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * nr) return;
+  const int64_t i = t % n;
+  const int k = (int)(t / n);
+  Y[i + k * ldy] *= colscale[k];
+}
+
+// dM_e = sum_k dZ[row_e][k] R[col_e][k]; dout_e = dM_e / A_ii (float)
+__global__ void dm_kernel(int64_t nnz, int nr, const int32_t* __restrict__ erow,
+                          const int32_t* __restrict__ col, const double* __restrict__ dZ,
+                          int64_t ldz, const double* __restrict__ R, int64_t ldr,
+                          const double* __restrict__ dinv, float* __restrict__ dout) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nnz) return;
+  const int i = erow[q], j = col[q];
+  double s = 0.0;
+  for (int k = 0; k < nr; ++k) s = fma(dZ[i + k * ldz], R[j + k * ldr], s);
+  dout[q] = (float)(s * dinv[i]);
+}
+
+// ---- backward ----------------------------------------------------------------------------
+// Weight-gradient partials: every block writes its partial sum of one weight group to
+// part[blockIdx][0..cnt) (fixed order), reduced by reduce_partials_kernel.
+__device__ __forceinline__ void block_partial_store(float* acc, int cnt, float* smem_red,
+                                                    float* part) {
+  // acc: per-warp values, lane-major: acc[k] belongs to (lane, k); reduce over warps
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per_lane = cnt / 32;
+  for (int k = 0; k < per_lane; ++k) smem_red[(warp * per_lane + k) * 32 + lane] = acc[k];
+  __syncthreads();
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const int k = t / 32, ln = t % 32;
+    float s = 0.f;
+    for (int w2 = 0; w2 < nw; ++w2) s += smem_red[(w2 * per_lane + k) * 32 + ln];
+    part[(int64_t)blockIdx.x * cnt + t] = s;
+  }
+  __syncthreads();
+}
+
+// decoder backward: grad wo/bo partials, de (edges), dh (nodes)
+__global__ void decode_back_edges_kernel(int64_t nnz, const int32_t* __restrict__ erow,
+                                         const int32_t* __restrict__ col, const float* __restrict__ e,
+                                         const float* __restrict__ h, const float* __restrict__ dout,
+                                         const __nv_bfloat16* __restrict__ w, float* __restrict__ de,
+                                         float* __restrict__ part) {
+  extern __shared__ float sred[];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float w0 = bf(w, OFF_WO + lane);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};  // g_wo[lane], g_wo[32+lane], g_wo[64+lane], g_bo (lane 0)
+  for (int64_t q = warp0; q < nnz; q += nwarps) {
+    const int i = erow[q], j = col[q];
+    const float d = dout[q];
+    acc[0] = fmaf(d, e[q * W + lane], acc[0]);
+    acc[1] = fmaf(d, h[(int64_t)i * W + lane], acc[1]);
+    acc[2] = fmaf(d, h[(int64_t)j * W + lane], acc[2]);
+    if (lane == 0) acc[3] += d;
+    de[q * W + lane] = d * w0;
+  }
+  block_partial_store(acc, 128, sred, part);
+}
+
+// dh_i = wo[32:64] * sum_{e in row i} dout_e + wo[64:96] * sum_{e in row i} dout_{tpos e}
+__global__ void decode_back_nodes_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                         const int32_t* __restrict__ tpos,
+                                         const float* __restrict__ dout,
+                                         const __nv_bfloat16* __restrict__ w, float* __restrict__ dh) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * W) return;
+  const int64_t i = t / W;
+  const int c = (int)(t % W);
+  float s1 = 0.f, s2 = 0.f;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    s1 += dout[e];
+    s2 += dout[tpos[e]];
+  }
+  dh[t] = bf(w, OFF_WO + W + c) * s1 + bf(w, OFF_WO + 2 * W + c) * s2;
+}
+
+// node update backward (layer l): warp per node.
+//   dzh = dh * [rh > 0];  g_Wh += dzh v^T (v = [h_l, agg_l]);  g_bh += dzh
+//   dv = Wh^T dzh;  dh_l = dh + dv[:32];  dagg = dv[32:]
+__global__ void node_back_kernel(int64_t n, const float* __restrict__ dh, const float* __restrict__ rh,
+                                 const float* __restrict__ hin, const float* __restrict__ agg,
+                                 const __nv_bfloat16* __restrict__ w, int l, float* __restrict__ dhl,
+                                 float* __restrict__ dagg, float* __restrict__ part) {
+  extern __shared__ float sred[];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // column `lane` and `32 + lane` of Wh (rows c = 0..31)
+  float wc[2 * W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    wc[c] = bf(w, off_wh(l) + c * 2 * W + lane);
+    wc[W + c] = bf(w, off_wh(l) + c * 2 * W + W + lane);
+  }
+  float g[2 * W + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * W + 1; ++k) g[k] = 0.f;
+  for (int64_t i = warp0; i < n; i += nwarps) {
+    const float dz = rh[i * W + lane] > 0.f ? dh[i * W + lane] : 0.f;
+    const float hv = hin[i * W + lane], av = agg[i * W + lane];
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      // g_Wh[lane][k] += dz * v[k],  v[k] = h[k], v[32+k] = agg[k]
+      const float hk = __shfl_sync(0xffffffffu, hv, k);
+      const float ak = __shfl_sync(0xffffffffu, av, k);
+      g[k] = fmaf(dz, hk, g[k]);
+      g[W + k] = fmaf(dz, ak, g[W + k]);
+      // dv[lane] = sum_c Wh[c][lane] dz_c
+      const float dzc = __shfl_sync(0xffffffffu, dz, k);
+      d0 = fmaf(wc[k], dzc, d0);
+      d1 = fmaf(wc[W + k], dzc, d1);
+    }
+    g[2 * W] += dz;
+    dhl[i * W + lane] = dh[i * W + lane] + d0;
+    dagg[i * W + lane] = d1;
+  }
+  // g holds row `lane` of the weight gradient (64 values) and the bias gradient;
+  // element (lane, k) of the partial sits at k * 32 + lane
+  block_partial_store(g, (2 * W + 1) * 32, sred, part);
+}
+
+// message backward (layer l): warp per edge.
+//   dm = de + dagg[i];  dzm = dm * [m > 0];  g_Wm += dzm u^T (u = [e_l, h_l[j]]);  g_bm += dzm
+//   du = Wm^T dzm;  de_l = de + du[:32];  dhj[e] = du[32:]  (gathered per node later)
+__global__ void message_back_kernel(int64_t nnz, const int32_t* __restrict__ erow,
+                                    const int32_t* __restrict__ col, const float* __restrict__ de,
+                                    const float* __restrict__ dagg, const float* __restrict__ m,
+                                    const float* __restrict__ ein, const float* __restrict__ h,
+                                    const __nv_bfloat16* __restrict__ w, int l,
+                                    float* __restrict__ del, float* __restrict__ dhj,
+                                    float* __restrict__ part) {
+  extern __shared__ float sred[];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float wc[2 * W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    wc[c] = bf(w, off_wm(l) + c * 2 * W + lane);
+    wc[W + c] = bf(w, off_wm(l) + c * 2 * W + W + lane);
+  }
+  float g[2 * W + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * W + 1; ++k) g[k] = 0.f;
+  for (int64_t q = warp0; q < nnz; q += nwarps) {
+    const int i = erow[q], j = col[q];
+    const float dmv = de[q * W + lane] + dagg[(int64_t)i * W + lane];
+    const float dz = m[q * W + lane] > 0.f ? dmv : 0.f;
+    const float ev = ein[q * W + lane], hv = h[(int64_t)j * W + lane];
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const float ek = __shfl_sync(0xffffffffu, ev, k);
+      const float hk = __shfl_sync(0xffffffffu, hv, k);
+      g[k] = fmaf(dz, ek, g[k]);
+      g[W + k] = fmaf(dz, hk, g[W + k]);
+      const float dzc = __shfl_sync(0xffffffffu, dz, k);
+      d0 = fmaf(wc[k], dzc, d0);
+      d1 = fmaf(wc[W + k], dzc, d1);
+    }
+    g[2 * W] += dz;
+    del[q * W + lane] = de[q * W + lane] + d0;
+    dhj[q * W + lane] = d1;
+  }
+  // g holds row `lane` of the weight gradient (64 values) and the bias gradient;
+  // element (lane, k) of the partial sits at k * 32 + lane
+  block_partial_store(g, (2 * W + 1) * 32, sred, part);
+}
+
+// dh_l[i] += sum over row i of dhj[tpos e]  (the column scatter, gathered per node)
+__global__ void gather_cols_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ tpos, const float* __restrict__ dhj,
+                                   float* __restrict__ dhl) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * W) return;
+  const int64_t i = t / W;
+  const int c = (int)(t % W);
+  float s = dhl[t];
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) s += dhj[(int64_t)tpos[e] * W + c];
+  dhl[t] = s;
+}
+
+// encoder backward: dz = d * [out > 0]; g_W[c][k] += dz x_k, g_b[c] += dz; one thread
+// per channel c and input k (plus bias), looping over all items in fixed order within
+// a block, blocks striding over items.
+__global__ void encode_back_kernel(int64_t cnt, int nin, const float* __restrict__ in,
+                                   const float* __restrict__ out, const float* __restrict__ d,
+                                   float* __restrict__ part) {
+  // thread layout: lane = channel c, warp w handles items w, w + nw, ...
+  extern __shared__ float sred[];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float acc[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+  for (int64_t it = warp0; it < cnt; it += nwarps) {
+    const float dz = out[it * W + lane] > 0.f ? d[it * W + lane] : 0.f;
+    for (int k = 0; k < nin; ++k) acc[k] = fmaf(dz, in[it * nin + k], acc[k]);
+    acc[nin] += dz;
+  }
+  block_partial_store(acc, 32 * 32, sred, part);
+}
+
+// grad[dst[k]] = sum over blocks of part[b][src[k]] (fixed block order)
+__global__ void reduce_partials_kernel(const float* __restrict__ part, int nblocks, int cnt,
+                                       const int* __restrict__ map_src, const int* __restrict__ map_dst,
+                                       int nmap, float* __restrict__ grad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nmap) return;
+  const int s = map_src[t];
+  float acc = 0.f;
+  for (int b = 0; b < nblocks; ++b) acc += part[(int64_t)b * cnt + s];
+  grad[map_dst[t]] = acc;
+}
+
+__global__ void adam_kernel(int np, float* __restrict__ th, const float* __restrict__ g,
+                            float* __restrict__ m1, float* __restrict__ m2, float lr, float b1,
+                            float b2, float eps, float c1, float c2, __nv_bfloat16* __restrict__ wbf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np) return;
+  const float gg = g[t];
+  const float a = b1 * m1[t] + (1.f - b1) * gg;
+  const float v = b2 * m2[t] + (1.f - b2) * gg * gg;
+  m1[t] = a;
+  m2[t] = v;
+  const float x = th[t] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+  th[t] = x;
+  wbf[t] = __float2bfloat16_rn(x);
+}
+
+__global__ void to_bf16_kernel(int np, const float* __restrict__ th, __nv_bfloat16* __restrict__ wbf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < np) wbf[t] = __float2bfloat16_rn(th[t]);
+}
+
+}  // namespace gnn
+}  // namespace rbo

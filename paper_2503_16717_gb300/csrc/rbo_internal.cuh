@@ -21,6 +21,10 @@ namespace rbo {
 // pass live in shared memory.
 constexpr int64_t MAX_SKETCH_DK = 12288;
 
+// Static scratch of rbo_gram_noalloc (see include/rbo.h).
+#define RBO_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define RBO_NOALLOC_MAX_AB 2048
+
 // ---- device status word -----------------------------------------------------------
 // Every kernel reads `code` first and returns at once when an earlier kernel of the
 // same call failed, so one host read at the end of a call reports the first failure.
@@ -126,6 +130,7 @@ struct RowPass {
   int acc_y = 0;                 // accumulate Y'^T Y'
   int sk_d = 0, sk_zeta = 0; uint64_t sk_seed = 0;  // accumulate S Y' (d x b)
   int mixed = 0;                 // float32 accumulation of X^T Y' and S Y'
+  int max_ctas = 0;              // cap on the grid (0: none); bounds the reduction scratch
   Epilogue epi;
 };
 
@@ -155,9 +160,11 @@ int residual_launch(const CsrDev& A, const double* b, const double* x, double* r
 int scale_columns_launch(const CsrDev& A, const double* dscale, double* val_out, cudaStream_t st);
 // dscale[i] = 1 / A[i][i]; status error when a diagonal entry is zero or missing
 int jacobi_launch(const CsrDev& A, double* dscale, DevStatus* status, cudaStream_t st);
-// y += Q z  (Q n x k, ld ldq; z device k)
+// y = Q z (accumulate 0) or y += Q z  (Q n x k, ld ldq; z device k)
 int gemv_update_launch(int64_t n, int k, const double* Q, int64_t ldq, const double* z, double* y,
-                       cudaStream_t st);
+                       int accumulate, cudaStream_t st);
+// x += diag(ds) t  (ds null: x += t)
+int axpy_scaled_launch(int64_t n, const double* ds, const double* t, double* x, cudaStream_t st);
 // mode 0: x = dscale .* y;  mode 1: x = y ./ dscale  (dscale null: copy)
 int scale_vec_launch(int64_t n, const double* dscale, const double* y, double* x, int mode,
                      cudaStream_t st);

@@ -26,14 +26,17 @@
 
 namespace rbo {
 
-constexpr int MAXO = 32;      // Z outputs per thread
+constexpr int CB = 8;         // Z columns per task (register block)
+constexpr int IPT = 4;        // Z tasks per thread
 constexpr int GROUP = 16;     // CTAs per first-level reduction group
 constexpr int NST = 2;        // pipeline stages
 
 struct PassDev {
   RowPass p;
   int T;              // rows per tile
+  int TP;             // shared-memory column stride of a tile (T + 2: fewer bank conflicts)
   int ntiles;
+  int items, tpo, tasks;  // Z work split: items = zr * ceil(b / CB), tpo row subsets
   int use_bulk;       // X/Y aligned for 16-byte bulk copies
   int zr, no;         // Z rows, Z outputs (zr * b)
   int L;              // partial length (no + d*b)
@@ -44,7 +47,7 @@ struct PassDev {
   unsigned* tickets;
   DevStatus* status;
   // shared memory layout (byte offsets from the dynamic base)
-  int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_red;
+  int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_ent, off_red;
 };
 
 // ------------------------------------------------------------------------------------
@@ -63,7 +66,8 @@ __device__ void tri_mult(const double* A, const double* B, int k, double* M) {
 }
 
 // R assembly after the final Cholesky of a block (R2 in shared memory, k x k).
-__device__ void assemble(const Epilogue& e, const double* R2, int k, double* scratch) {
+__device__ void assemble(const Epilogue& e, const double* R2, int k, double* scratch,
+                         DevStatus* status) {
   if (e.asm_op == ASM_NONE) return;
   double* Rf = e.Rfull;
   const int ld = e.ldR, p = e.p, c0 = e.col0;
@@ -74,6 +78,25 @@ __device__ void assemble(const Epilogue& e, const double* R2, int k, double* scr
     }
     __syncthreads();
     return;
+  }
+  // Loss of orthogonality: W~ = Qh - Q C2 is orthonormal up to O(eps kappa) terms
+  // when the first intra-block step worked, so R2 = chol(W~^T W~) is close to I.
+  // A large deviation means that step failed (the block is numerically rank
+  // deficient at the working precision) and the final CholQR cannot repair it;
+  // report instead of returning a non-orthogonal Q.
+  if (threadIdx.x == 0) {
+    double dev = 0.0;
+    for (int t = 0; t < k * k; ++t) {
+      const int i = t % k, c = t / k;
+      if (i <= c) dev = fmax(dev, fabs(R2[t] - (i == c ? 1.0 : 0.0)));
+    }
+    if (!(dev <= 0.5)) {
+      if (atomicCAS(&status->code, 0, RBO_ERR_LOST_ORTHOGONALITY) == 0) {
+        status->block = e.block;
+        status->column = -1;
+        status->stage = RBO_STAGE_FINAL;
+      }
+    }
   }
   // M = R' * (R_hat or T)
   double* M = scratch;  // k x k
@@ -149,7 +172,7 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
       if (e.out_r != nullptr)
         for (int t = threadIdx.x; t < b * b; t += blockDim.x) e.out_r[t] = G[t];
       __syncthreads();
-      assemble(e, G, b, sm + b * b);
+      assemble(e, G, b, sm + b * b, P.status);
       break;
     }
     case EPI_HH: {
@@ -246,7 +269,7 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
   if (read_code(P.status) != 0) return;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int T = P.T, a = rp.a, b = rp.b;
+  const int T = P.T, TP = P.TP, a = rp.a, b = rp.b;
   const int ax = rp.acc_x ? a : 0;
   const int64_t n = rp.n;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -255,6 +278,7 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
   double* dinv = reinterpret_cast<double*>(smem + P.off_dinv);
   double* skd = reinterpret_cast<double*>(smem + P.off_sk);
   float* skf = reinterpret_cast<float*>(smem + P.off_sk);
+  int* ent = reinterpret_cast<int*>(smem + P.off_ent);
   const int d = rp.sk_d;
   const bool do_sk = d > 0;
 
@@ -284,20 +308,23 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
   }
   __syncthreads();
 
-  // per-thread Z outputs
-  double acc[MAXO];
-  float accf[MAXO];
+  // Z tasks: item = (Z row i, block of up to CB columns), split over `tpo` row
+  // subsets; thread t owns tasks t, t + NT, ... (at most IPT)
+  double acc[IPT][CB];
+  float accf[IPT][CB];
 #pragma unroll
-  for (int j = 0; j < MAXO; ++j) {
-    acc[j] = 0.0;
-    accf[j] = 0.0f;
-  }
+  for (int k = 0; k < IPT; ++k)
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      acc[k][c] = 0.0;
+      accf[k][c] = 0.0f;
+    }
 
   const int ncol_tile = (a + b);
   auto stage_X = [&](int s) {
     return reinterpret_cast<double*>(smem + P.off_stage + (size_t)s * P.stage_bytes);
   };
-  auto stage_Y = [&](int s) { return stage_X(s) + (size_t)a * T; };
+  auto stage_Y = [&](int s) { return stage_X(s) + (size_t)a * TP; };
 
   // bulk-copy a full tile into stage s (thread 0 only)
   auto issue_tile = [&](int tile, int s) {
@@ -306,8 +333,10 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
     double* ys = stage_Y(s);
     const uint32_t bytes = (uint32_t)T * 8u;
     mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile);
-    for (int i = 0; i < a; ++i) bulk_copy_g2s(xs + (size_t)i * T, rp.X + i * rp.ldx + r0, bytes, &bars[s]);
-    for (int c = 0; c < b; ++c) bulk_copy_g2s(ys + (size_t)c * T, rp.Y + c * rp.ldy + r0, bytes, &bars[s]);
+    for (int i = 0; i < a; ++i)
+      bulk_copy_g2s(xs + (size_t)i * TP, rp.X + i * rp.ldx + r0, bytes, &bars[s]);
+    for (int c = 0; c < b; ++c)
+      bulk_copy_g2s(ys + (size_t)c * TP, rp.Y + c * rp.ldy + r0, bytes, &bars[s]);
   };
   auto bulk_ok = [&](int tile) {
     return P.use_bulk && ((int64_t)(tile + 1) * T <= n);
@@ -336,7 +365,7 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
         int col = t / T, r = t % T;
         double v = 0.0;
         if (r < rows) v = (col < a) ? rp.X[col * rp.ldx + r0 + r] : rp.Y[(col - a) * rp.ldy + r0 + r];
-        xs[t] = v;  // X and Y stages are contiguous
+        xs[(size_t)col * TP + r] = v;  // X and Y stages are contiguous
       }
       __syncthreads();
     }
@@ -351,23 +380,44 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
       issue_tile(nxt, s ^ 1);
     }
 
+    // sketch entries of the tile's rows (integer hash; -1 marks rows past n)
+    if (do_sk) {
+      for (int r = tid; r < T; r += NT) {
+        int ix[ZMAX], ng[ZMAX];
+#pragma unroll
+        for (int t = 0; t < ZMAX; ++t) { ix[t] = 0; ng[t] = 0; }
+        const bool valid = r < rows;
+        if (valid && !sketch_column(rp.sk_seed, (uint64_t)(r0 + r), d, rp.sk_zeta, ix, ng))
+          set_error(P.status, RBO_ERR_SKETCH, 2);
+#pragma unroll
+        for (int t = 0; t < ZMAX; ++t)
+          if (t < rp.sk_zeta) ent[r * rp.sk_zeta + t] = valid ? (ix[t] * 2 + ng[t]) : -1;
+      }
+    }
+
     // ---- phase A: y' = transform(y), in place in the Y stage --------------------
-    const int tpr = NT / T;          // threads per row
-    const int r = tid % T, q = tid / T;
     auto tri_solve = [&]() {
-      if (q == 0) {
+      for (int r = tid; r < T; r += NT) {
         for (int c = 0; c < b; ++c) {
-          double v = ys[c * T + r];
-          for (int i = 0; i < c; ++i) v = fma(-ys[i * T + r], Ts[i + c * b], v);
-          ys[c * T + r] = v * dinv[c];
+          double v = ys[c * TP + r];
+          for (int i = 0; i < c; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
+          ys[c * TP + r] = v * dinv[c];
         }
       }
     };
     auto project = [&]() {
-      for (int c = q; c < b; c += tpr) {
-        double v = ys[c * T + r];
-        for (int i = 0; i < a; ++i) v = fma(-xs[i * T + r], Cs[i + c * a], v);
-        ys[c * T + r] = v;
+      // one (row, column) element per task; two interleaved partial sums
+      for (int t = tid; t < T * b; t += NT) {
+        const int r = t % T, c = t / T;
+        const double* cc = Cs + (size_t)c * a;
+        double v0 = ys[c * TP + r], v1 = 0.0;
+        int i = 0;
+        for (; i + 1 < a; i += 2) {
+          v0 = fma(-xs[i * TP + r], cc[i], v0);
+          v1 = fma(-xs[(i + 1) * TP + r], cc[i + 1], v1);
+        }
+        if (i < a) v0 = fma(-xs[i * TP + r], cc[i], v0);
+        ys[c * TP + r] = v0 + v1;
       }
     };
     if (rp.Tri && rp.tri_first) {
@@ -385,7 +435,7 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
     if (rp.write_y) {
       for (int t = tid; t < b * T; t += NT) {
         int c = t / T, rr = t % T;
-        if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = ys[t];
+        if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = ys[(size_t)c * TP + rr];
       }
     }
 
@@ -395,61 +445,59 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
       // element t sits in the first 4 bytes of its double slot
       __syncthreads();
       for (int t = tid; t < ncol_tile * T; t += NT) {
-        float f = f64_to_f32_int(xs[t]);
-        reinterpret_cast<float*>(xs + t)[0] = f;
+        const size_t e = (size_t)(t / T) * TP + (t % T);
+        float f = f64_to_f32_int(xs[e]);
+        reinterpret_cast<float*>(xs + e)[0] = f;
       }
       __syncthreads();
     }
     if (P.no > 0) {
-      if (MIXED) {
 #pragma unroll
-        for (int j = 0; j < MAXO; ++j) {
-          const int o = tid + j * NT;
-          if (o < P.no) {
-            const int i = o / b, c = o % b;
-            const double* zsrc = (i < ax) ? xs + (size_t)i * T : ys + (size_t)(i - ax) * T;
-            const double* ysrc = ys + (size_t)c * T;
-            float sacc = accf[j];
-            for (int rr = 0; rr < T; ++rr)
-              sacc = fmaf(reinterpret_cast<const float*>(zsrc + rr)[0],
-                          reinterpret_cast<const float*>(ysrc + rr)[0], sacc);
-            accf[j] = sacc;
-          }
-        }
-      } else {
+      for (int k = 0; k < IPT; ++k) {
+        const int task = tid + k * NT;
+        if (task < P.tasks) {
+          const int item = task % P.items, g = task / P.items;
+          const int i = item % P.zr, c0 = (item / P.zr) * CB;
+          const int cw = min(CB, b - c0);
+          const double* zsrc = (i < ax) ? xs + (size_t)i * TP : ys + (size_t)(i - ax) * TP;
+          const double* ysrc = ys + (size_t)c0 * TP;
+          if (MIXED) {
+            for (int rr = g; rr < T; rr += P.tpo) {
+              const float z = reinterpret_cast<const float*>(zsrc + rr)[0];
 #pragma unroll
-        for (int j = 0; j < MAXO; ++j) {
-          const int o = tid + j * NT;
-          if (o < P.no) {
-            const int i = o / b, c = o % b;
-            const double* zsrc = (i < ax) ? xs + (size_t)i * T : ys + (size_t)(i - ax) * T;
-            const double* ysrc = ys + (size_t)c * T;
-            double sacc = acc[j];
-            for (int rr = 0; rr < T; ++rr) sacc = fma(zsrc[rr], ysrc[rr], sacc);
-            acc[j] = sacc;
+              for (int c = 0; c < CB; ++c)
+                if (c < cw)
+                  accf[k][c] = fmaf(z, reinterpret_cast<const float*>(ysrc + (size_t)c * TP + rr)[0],
+                                    accf[k][c]);
+            }
+          } else {
+            for (int rr = g; rr < T; rr += P.tpo) {
+              const double z = zsrc[rr];
+#pragma unroll
+              for (int c = 0; c < CB; ++c)
+                if (c < cw) acc[k][c] = fma(z, ysrc[(size_t)c * TP + rr], acc[k][c]);
+            }
           }
         }
       }
     }
-    // ---- phase B': sketch S Y' (warp-private copies, lane-ordered collisions) -----
-    if (do_sk && warp < P.nsw) {
-      const int rr = warp * 32 + lane;
-      const bool valid = rr < rows && rr < T;
-      int idx[ZMAX], neg[ZMAX];
-#pragma unroll
-      for (int t = 0; t < ZMAX; ++t) {
-        idx[t] = 0;
-        neg[t] = 0;
-      }
-      if (valid) {
-        if (!sketch_column(rp.sk_seed, (uint64_t)(r0 + rr), d, rp.sk_zeta, idx, neg))
-          set_error(P.status, RBO_ERR_SKETCH, 2);
-      }
-      const unsigned lt_mask = (1u << lane) - 1u;
-#pragma unroll
-      for (int t = 0; t < ZMAX; ++t) {
-        if (t < rp.sk_zeta) {
-          const int key = valid ? idx[t] : -1 - lane;
+    // ---- phase B': sketch S Y' ---------------------------------------------------
+    // (row, slot) pairs of the tile are scattered by the first nsw warps into
+    // warp-private copies; lanes of a warp that hit the same sketch row add in lane
+    // order, so every copy is summed in a fixed order (deterministic).
+    if (do_sk) {
+      __syncthreads();  // entries of this tile complete
+      if (warp < P.nsw) {
+        const int zeta = rp.sk_zeta;
+        const int npair = T * zeta;
+        const unsigned lt_mask = (1u << lane) - 1u;
+        for (int p0 = warp * 32; p0 < npair; p0 += P.nsw * 32) {
+          const int pr = p0 + lane;
+          const int ev = pr < npair ? ent[pr] : -1;
+          const int rr = pr / zeta;
+          const bool valid = ev >= 0;
+          const int ix = ev >> 1;
+          const int key = valid ? ix : -1 - lane;
           const unsigned grp = __match_any_sync(0xffffffffu, key);
           const int rank = __popc(grp & lt_mask);
           const int maxrank = __reduce_max_sync(0xffffffffu, (unsigned)rank);
@@ -458,14 +506,14 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
               if (MIXED) {
                 float* cp = skf + (size_t)warp * d * b;
                 for (int c = 0; c < b; ++c) {
-                  float yv = reinterpret_cast<const float*>(ys + (size_t)c * T + rr)[0];
-                  cp[idx[t] + c * d] += neg[t] ? -yv : yv;
+                  const float yv = reinterpret_cast<const float*>(ys + (size_t)c * TP + rr)[0];
+                  cp[ix + c * d] += (ev & 1) ? -yv : yv;
                 }
               } else {
                 double* cp = skd + (size_t)warp * d * b;
                 for (int c = 0; c < b; ++c) {
-                  double yv = ys[(size_t)c * T + rr];
-                  cp[idx[t] + c * d] += neg[t] ? -yv : yv;
+                  const double yv = ys[(size_t)c * TP + rr];
+                  cp[ix + c * d] += (ev & 1) ? -yv : yv;
                 }
               }
             }
@@ -480,10 +528,24 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
   // ---------------- partials + fixed-order two-level tree -------------------------
   if (P.L == 0) return;
   double* mypart = P.partials + (size_t)blockIdx.x * P.L;
+  if (P.no > 0) {
+    // combine the tpo row-subset partial sums of every item in a fixed order
+    double* comb = reinterpret_cast<double*>(smem + P.off_stage);  // tasks x CB
 #pragma unroll
-  for (int j = 0; j < MAXO; ++j) {
-    const int o = tid + j * NT;
-    if (o < P.no) mypart[o] = MIXED ? (double)accf[j] : acc[j];
+    for (int k = 0; k < IPT; ++k) {
+      const int task = tid + k * NT;
+      if (task < P.tasks)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) comb[(size_t)task * CB + c] = MIXED ? (double)accf[k][c] : acc[k][c];
+    }
+    __syncthreads();
+    for (int o = tid; o < P.no; o += NT) {
+      const int i = o / b, c = o % b;
+      const int item = (c / CB) * P.zr + i, cc = c % CB;
+      double sum = 0.0;
+      for (int g = 0; g < P.tpo; ++g) sum += comb[(size_t)(g * P.items + item) * CB + cc];
+      mypart[o] = sum;
+    }
   }
   if (do_sk) {
     for (int t = tid; t < d * b; t += NT) {
@@ -616,30 +678,48 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   if (rp.sk_d > DMAX || rp.sk_zeta > ZMAX) return RBO_ERR_ARG;
   const int zr = (rp.acc_x ? rp.a : 0) + (rp.acc_y ? rp.b : 0);
   const int no = zr * rp.b;
-  if (no > MAXO * NT) return RBO_ERR_ARG;
+  if (no > 8192) return RBO_ERR_ARG;
   const int dsk = rp.sk_d > 0 ? rp.sk_d : 0;
   const int L = no + dsk * rp.b;
   const int mixed = rp.mixed ? 1 : 0;
+  // Z work split: items (Z row, block of CB columns), tpo row subsets per item
+  const int items = zr * ((rp.b + CB - 1) / CB);
+  if (items > IPT * NT) return RBO_ERR_ARG;
 
-  // choose the tile height: largest of 64/32 that fits
+  // choose the tile height: largest of 64/32/16 that fits
   int T = 64;
   size_t smem = 0;
-  int nsw = 0;
-  size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_sk = 0, off_red = 0;
+  int nsw = 0, tpo = 1, tasks = 0;
+  size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_sk = 0,
+         off_ent = 0, off_red = 0;
   for (;;) {
-    nsw = dsk > 0 ? std::max(1, T / 32) : 0;
+    tpo = 1;
+    if (items > 0)
+      while (items * tpo * 2 <= NT && tpo * 2 <= T / 4) tpo *= 2;
+    tasks = items * tpo;
+    const int TP = T + 2;
+    // sketch copies: one per scatter warp, up to 4 (one per SM sub-partition) while
+    // they take at most 96 KB
+    nsw = 0;
+    if (dsk > 0) {
+      const size_t one = (size_t)dsk * rp.b * (mixed ? 4 : 8);
+      nsw = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / std::max<size_t>(one, 1)));
+    }
     off_stage = 64;
-    stage_bytes = (size_t)(rp.a + rp.b) * T * 8;
+    stage_bytes = (size_t)(rp.a + rp.b) * TP * 8;
     size_t o = off_stage + NST * stage_bytes;
     off_c = o; o += (rp.C ? (size_t)rp.a * rp.b * 8 : 0);
     off_tri = o; o += (rp.Tri ? (size_t)rp.b * rp.b * 8 : 0);
     off_dinv = o; o += (rp.Tri ? (size_t)rp.b * 8 : 0);
     o = (o + 15) & ~size_t(15);
     off_sk = o; o += (size_t)nsw * dsk * rp.b * (mixed ? 4 : 8);
+    o = (o + 15) & ~size_t(15);
+    off_ent = o; o += (dsk > 0 ? (size_t)T * ZMAX * 4 : 0);
     size_t loop_bytes = o;
+    size_t comb_bytes = off_stage + (size_t)tasks * CB * 8;
     off_red = 64;
     size_t epi_bytes = off_red + ((size_t)L + 2) * 8 + epilogue_doubles(rp, zr) * 8;
-    smem = std::max(loop_bytes, epi_bytes);
+    smem = std::max(std::max(loop_bytes, epi_bytes), comb_bytes);
     if (smem <= 220 * 1024 || T == 16) break;
     T /= 2;
   }
@@ -648,13 +728,18 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   const int ntiles = (int)((rp.n + T - 1) / T);
   const int occ = mixed ? occupancy<true>((int)smem) : occupancy<false>((int)smem);
   int G = std::min(ntiles, occ * sm_count());
+  if (rp.max_ctas > 0) G = std::min(G, rp.max_ctas);
   if (G < 1) G = 1;
   const int ngroups = (G + GROUP - 1) / GROUP;
 
   PassDev P;
   P.p = rp;
   P.T = T;
+  P.TP = T + 2;
   P.ntiles = ntiles;
+  P.items = items;
+  P.tpo = tpo;
+  P.tasks = tasks;
   const bool alignedX = rp.a == 0 || (((uintptr_t)rp.X & 15) == 0 && (rp.ldx % 2) == 0);
   const bool alignedY = (((uintptr_t)rp.Y & 15) == 0 && (rp.ldy % 2) == 0);
   P.use_bulk = (alignedX && alignedY) ? 1 : 0;
@@ -670,6 +755,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.off_tri = (int)off_tri;
   P.off_dinv = (int)off_dinv;
   P.off_sk = (int)off_sk;
+  P.off_ent = (int)off_ent;
   P.off_red = (int)off_red;
   P.partials = nullptr;
   P.gpart = nullptr;

@@ -137,9 +137,10 @@ int jacobi_launch(const CsrDev& A, double* dscale, DevStatus* status, cudaStream
   return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
 }
 
-// y += Q z: one thread per row, z in shared memory
+// y = Q z (accumulate = 0) or y += Q z: one thread per row, z in shared memory
 __global__ void gemv_update_kernel(int64_t n, int k, const double* __restrict__ Q, int64_t ldq,
-                                   const double* __restrict__ z, double* __restrict__ y) {
+                                   const double* __restrict__ z, double* __restrict__ y,
+                                   int accumulate) {
   __shared__ double zs[256];
   for (int t = threadIdx.x; t < k; t += blockDim.x) zs[t] = z[t];
   __syncthreads();
@@ -147,14 +148,28 @@ __global__ void gemv_update_kernel(int64_t n, int k, const double* __restrict__ 
   if (i >= n) return;
   double s = 0.0;
   for (int c = 0; c < k; ++c) s = fma(Q[i + c * ldq], zs[c], s);
-  y[i] += s;
+  y[i] = accumulate ? y[i] + s : s;
+}
+
+// x += D t  (D = diag(ds), or the identity when ds is null)
+__global__ void axpy_scaled_kernel(int64_t n, const double* __restrict__ ds,
+                                   const double* __restrict__ t, double* __restrict__ x) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] += ds ? ds[i] * t[i] : t[i];
+}
+
+int axpy_scaled_launch(int64_t n, const double* ds, const double* t, double* x, cudaStream_t st) {
+  if (n <= 0) return RBO_OK;
+  axpy_scaled_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ds, t, x);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
 }
 
 int gemv_update_launch(int64_t n, int k, const double* Q, int64_t ldq, const double* z, double* y,
-                       cudaStream_t st) {
+                       int accumulate, cudaStream_t st) {
   if (n <= 0 || k <= 0) return RBO_OK;
   if (k > 256) return RBO_ERR_ARG;
-  gemv_update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, k, Q, ldq, z, y);
+  gemv_update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, k, Q, ldq, z, y, accumulate);
   return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
 }
 

@@ -169,3 +169,103 @@ def glued_blocks_torch(n: int, nblocks: int, s: int, kappa: float, seed: int,
         c += s
         del G, U
     return V  # (ncols, n) row-major == n x ncols column-major with ld = n
+
+
+# ---- convection-diffusion families (learned-preconditioner and stress workloads) ----------
+def _smooth_gaussian_field(shape, corr: float, rng) -> np.ndarray:
+    """Unit-variance Gaussian random field with covariance ~ exp(-r^2 / (2 corr^2)):
+    white noise filtered (periodically) by a Gaussian of standard deviation
+    corr / sqrt(2) cells, then renormalised."""
+    from scipy import ndimage
+    g = rng.standard_normal(shape)
+    f = ndimage.gaussian_filter(g, sigma=corr / np.sqrt(2.0), mode="wrap")
+    return (f - f.mean()) / f.std()
+
+
+def convdiff2d_csr(N: int, seed: int, sigma: float = 1.0, corr: float = 32.0,
+                   pe_range=(10.0, 1000.0)):
+    """2D convection-diffusion -div(k grad u) + w . grad u on the unit square, N x N
+    interior cells, Dirichlet boundary, 5-point stencil: diffusion with harmonic-mean
+    face diffusivities, first-order upwind convection.  k = exp(sigma g) with g a
+    unit-variance Gaussian field of correlation length `corr` cells; w constant with
+    a random angle and Peclet number |w| L / mean(k) uniform in `pe_range` (L = 1).
+    Returns (CSR, meta)."""
+    rng = np.random.default_rng(seed)
+    k = np.exp(sigma * _smooth_gaussian_field((N, N), corr, rng))   # k[y, x]
+    theta = rng.uniform(0.0, 2.0 * np.pi)
+    pe = rng.uniform(*pe_range)
+    wmag = pe * k.mean()
+    wx, wy = wmag * np.cos(theta), wmag * np.sin(theta)
+    h = 1.0 / (N + 1)
+    idx = np.arange(N * N).reshape(N, N)
+    rows, cols, vals = [], [], []
+    diag = np.zeros((N, N))
+
+    def face(a, b):
+        return 2.0 * a * b / (a + b)
+
+    # x-direction faces (between (y, x) and (y, x+1)), y-direction faces
+    for axis, wcomp in ((1, wx), (0, wy)):
+        kn = np.roll(k, -1, axis=axis)
+        kp = np.roll(k, 1, axis=axis)
+        fplus = face(k, kn)   # face to the +1 neighbour
+        fminus = face(k, kp)  # face to the -1 neighbour
+        last = [slice(None)] * 2
+        first = [slice(None)] * 2
+        last[axis] = N - 1
+        first[axis] = 0
+        fplus[tuple(last)] = k[tuple(last)]     # boundary faces: the cell's own value
+        fminus[tuple(first)] = k[tuple(first)]
+        diag += (fplus + fminus) / h**2
+        conv_p = max(-wcomp, 0.0) / h           # upwind from the + side (w < 0)
+        conv_m = max(wcomp, 0.0) / h            # upwind from the - side (w > 0)
+        diag += conv_p + conv_m
+        # off-diagonals to the +1 neighbour
+        sel = [slice(None)] * 2
+        sel[axis] = slice(0, N - 1)
+        sel = tuple(sel)
+        nb = np.roll(idx, -1, axis=axis)
+        rows.append(idx[sel].ravel())
+        cols.append(nb[sel].ravel())
+        vals.append((-fplus[sel] / h**2 - conv_p).ravel())
+        sel2 = [slice(None)] * 2
+        sel2[axis] = slice(1, N)
+        sel2 = tuple(sel2)
+        nb2 = np.roll(idx, 1, axis=axis)
+        rows.append(idx[sel2].ravel())
+        cols.append(nb2[sel2].ravel())
+        vals.append((-fminus[sel2] / h**2 - conv_m).ravel())
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    import scipy.sparse as sp
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(N * N, N * N))
+    return CSR.from_scipy(A), {"peclet": pe, "theta": theta, "wx": wx, "wy": wy, "seed": seed}
+
+
+def convdiff3d_csr(N: int, seed: int, aniso=(1.0, 1.0, 1e-3), pe: float = 100.0):
+    """3D convection-diffusion, 7-point, constant anisotropic diffusion `aniso`,
+    first-order upwind convection with a random direction and |w| = pe (L = 1,
+    unit mean diffusivity), Dirichlet, N^3 interior cells."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(3)
+    w = pe * v / np.linalg.norm(v)
+    h = 1.0 / (N + 1)
+    import scipy.sparse as sp
+    e = np.ones(N)
+    I = sp.identity(N, format="csr")
+    mats = []
+    for ax in range(3):
+        T = sp.diags([-e[:-1], 2 * e, -e[:-1]], [-1, 0, 1]) * (aniso[ax] / h**2)
+        wc = w[ax]
+        if wc > 0:
+            C = sp.diags([-e[:-1], e], [-1, 0]) * (wc / h)
+        else:
+            C = sp.diags([e, -e[:-1]], [0, 1]) * (-wc / h)
+        D1 = (T + C).tocsr()
+        ops = [I, I, I]
+        ops[2 - ax] = D1   # x fastest
+        mats.append(sp.kron(sp.kron(ops[0], ops[1]), ops[2]))
+    A = (mats[0] + mats[1] + mats[2]).tocsr()
+    return CSR.from_scipy(A), {"w": w.tolist(), "seed": seed}
