@@ -85,6 +85,18 @@ SIGNATURES = {
     "rbo_mpk_csr": (C.c_int, [C.POINTER(Csr), _vp, _i32, _vp, _vp, _i64, _vp]),
     "rbo_sstep_gmres": (C.c_int, [C.POINTER(Csr), _vp, _vp, _i32, _i32, _i32, C.c_double, _vp,
                                   C.POINTER(Opts), C.POINTER(Info), _vp]),
+    "rbo_sstep_gmres_precond": (C.c_int, [C.POINTER(Csr), _vp, _vp, _vp, _i32, _i32, _i32,
+                                          C.c_double, _vp, C.POINTER(Opts), C.POINTER(Info), _vp]),
+    "rbo_gnn_param_count": (C.c_int, []),
+    "rbo_gnn_create": (C.c_int, [_u64, C.POINTER(_vp)]),
+    "rbo_gnn_destroy": (C.c_int, [_vp]),
+    "rbo_gnn_set_params": (C.c_int, [_vp, _vp]),
+    "rbo_gnn_get_params": (C.c_int, [_vp, _vp]),
+    "rbo_gnn_infer": (C.c_int, [_vp, C.POINTER(Csr), _vp, _vp]),
+    "rbo_gnn_loss_grad": (C.c_int, [_vp, C.POINTER(Csr), _vp, _i32, _i64, C.POINTER(C.c_double),
+                                    _vp, _vp]),
+    "rbo_gnn_train_step": (C.c_int, [_vp, C.POINTER(Csr), _vp, _i32, _i64, C.c_float,
+                                     C.POINTER(C.c_double), _vp]),
     "rbo_profile_enable": (C.c_int, [C.c_int]),
     "rbo_profile_reset": (C.c_int, []),
     "rbo_profile_read": (C.c_int, [_i32, C.POINTER(C.c_int64), C.POINTER(C.c_double),
@@ -291,8 +303,10 @@ def mpk_csr(A: DeviceCSR, v0, s: int, V=None, dscale=None):
 def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int = 60,
                 tol: float = 1e-10, sk: Sketch | None = None, precision: int = PREC_FP64,
                 precond: int = 1, max_restarts: int = 0, history_cap: int = 4096,
-                raise_on_error: bool = False):
-    """s-step GMRES(m); returns (x, info).  s_hat in (0, s) -> one-stage, else two-stage."""
+                M=None, raise_on_error: bool = False):
+    """s-step GMRES(m); returns (x, info).  s_hat in (0, s] -> one-stage, else two-stage.
+    ``M``: optional device tensor of preconditioner values on A's pattern (right
+    preconditioner; overrides ``precond``)."""
     torch = _torch()
     if x is None:
         x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
@@ -302,14 +316,72 @@ def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int =
     info.history = C.cast(hist, C.POINTER(C.c_double))
     info.history_cap = history_cap
     o = _opts(precision, False, INTRA_RANDCHOLQR, max_restarts, precond)
-    code = lib.rbo_sstep_gmres(C.byref(st), _vec(b, "b"), _vec(x, "x"), s, s_hat, m, tol,
-                               sk.handle if sk is not None else None, C.byref(o), C.byref(info),
-                               _stream())
+    skh = sk.handle if sk is not None else None
+    if M is not None:
+        code = lib.rbo_sstep_gmres_precond(C.byref(st), _vec(M, "M"), _vec(b, "b"), _vec(x, "x"), s,
+                                           s_hat, m, tol, skh, C.byref(o), C.byref(info), _stream())
+    else:
+        code = lib.rbo_sstep_gmres(C.byref(st), _vec(b, "b"), _vec(x, "x"), s, s_hat, m, tol, skh,
+                                   C.byref(o), C.byref(info), _stream())
     d = info_dict(info)
     d["history"] = [(int(hist[2 * i]), float(hist[2 * i + 1])) for i in range(info.history_len)]
     if code != OK and raise_on_error:
         raise RboError(code, "sstep_gmres", info)
     return x, d
+
+
+# ---- learned SPAI preconditioner -----------------------------------------------------------
+class GNN:
+    """Handle of the learned sparse-approximate-inverse network (BF16 weights, FP32
+    master weights and Adam state on the device)."""
+
+    def __init__(self, seed: int = 0):
+        h = C.c_void_p()
+        _check(lib.rbo_gnn_create(seed, C.byref(h)), "gnn_create")
+        self.handle = h
+        self.nparam = lib.rbo_gnn_param_count()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.rbo_gnn_destroy(h)
+            self.handle = None
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparam, dtype=np.float32)
+        _check(lib.rbo_gnn_get_params(self.handle, out.ctypes.data_as(C.c_void_p)), "gnn_get_params")
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != self.nparam:
+            raise ValueError("wrong parameter count")
+        _check(lib.rbo_gnn_set_params(self.handle, th.ctypes.data_as(C.c_void_p)), "gnn_set_params")
+
+    def infer(self, A: "DeviceCSR"):
+        torch = _torch()
+        M = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+        st = A.struct()
+        _check(lib.rbo_gnn_infer(self.handle, C.byref(st), C.c_void_p(M.data_ptr()), _stream()),
+               "gnn_infer")
+        return M
+
+    def loss_grad(self, A: "DeviceCSR", R):
+        pr, n, nr, ldr = _mat(R, "R")
+        st = A.struct()
+        loss = C.c_double()
+        g = np.zeros(self.nparam, dtype=np.float32)
+        _check(lib.rbo_gnn_loss_grad(self.handle, C.byref(st), pr, nr, ldr, C.byref(loss),
+                                     g.ctypes.data_as(C.c_void_p), _stream()), "gnn_loss_grad")
+        return loss.value, g
+
+    def train_step(self, A: "DeviceCSR", R, lr: float = 1e-3) -> float:
+        pr, n, nr, ldr = _mat(R, "R")
+        st = A.struct()
+        loss = C.c_double()
+        _check(lib.rbo_gnn_train_step(self.handle, C.byref(st), pr, nr, ldr, lr, C.byref(loss),
+                                      _stream()), "gnn_train_step")
+        return loss.value
 
 
 PROF_ROWPASS, PROF_SPMV, PROF_VECTOR = 0, 1, 2
