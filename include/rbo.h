@@ -132,6 +132,26 @@ int rbo_sketch_apply(rbo_sketch sk, int64_t n, int32_t k, const double* W, int64
 int rbo_gram(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, const double* Y,
              int64_t ldy, double* C, void* stream);
 
+/* ---- tall-skinny Gram without allocation -------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that cannot
+ * let a library allocate device memory -- applications whose HBM is owned by another
+ * allocator (a framework pool that has reserved the free memory), loops that must not
+ * pay the implicit synchronisation of cudaMalloc/cudaFree, programs with a memory
+ * budget fixed at start-up.
+ * C = X^T Y like rbo_gram, but C is a caller-owned DEVICE array (a x b, column-major,
+ * ld a) and the call allocates nothing: its reduction scratch is one static 4 MiB
+ * device array (RBO_NOALLOC_SCRATCH_BYTES) that every GPU loading the library keeps
+ * until the process exits.  Limits: a <= 128, b <= 64, a * b <= 2048 (larger shapes
+ * return RBO_ERR_ARG).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents
+ * (each call re-zeroes the counters it needs), so calls that overlap on the GPU --
+ * different streams or host threads at the same time -- race and must be
+ * serialised by the caller.  Synchronises `stream` once to read the status word.
+ * Errors: RBO_ERR_ARG, RBO_ERR_NO_DEVICE, RBO_ERR_TIMEOUT, RBO_ERR_CUDA.            */
+int rbo_gram_noalloc(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b,
+                     const double* Y, int64_t ldy, double* C, void* stream);
+
 /* ---- block orthogonalization ------------------------------------------------------
  * V (n x ncols, device, ld ldv) is overwritten by Q; R (ncols x ncols, column-major,
  * ld ldr >= ncols, caller-owned HOST array) receives the upper-triangular factor.

@@ -76,6 +76,7 @@ SIGNATURES = {
     "rbo_sketch_entries": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "rbo_sketch_apply": (C.c_int, [_vp, _i64, _i32, _vp, _i64, _dp, _i32, _vp]),
     "rbo_gram": (C.c_int, [_i64, _i32, _vp, _i64, _i32, _vp, _i64, _dp, _vp]),
+    "rbo_gram_noalloc": (C.c_int, [_i64, _i32, _vp, _i64, _i32, _vp, _i64, _vp, _vp]),
     "rbo_block_orth_one_stage": (C.c_int, [_vp, _i64, _i32, _i32, _vp, _i64, _dp, _i64,
                                            C.POINTER(Opts), C.POINTER(Info), _vp]),
     "rbo_block_orth_two_stage": (C.c_int, [_vp, _i64, _i32, _i32, _i32, _vp, _i64, _dp, _i64,
