@@ -94,6 +94,13 @@ typedef struct rbo_info {
                                 pairs, one per restart                                 */
   int32_t history_cap;       /* capacity of `history` in pairs                         */
   int32_t history_len;       /* pairs written                                          */
+  double* resid;             /* GMRES, optional caller DEVICE buffer (n x resid_cap,
+                                ld resid_ld): the true residual b - A x at the start
+                                of each restart cycle (training data for the learned
+                                preconditioner)                                        */
+  int64_t resid_ld;
+  int32_t resid_cap;
+  int32_t resid_len;         /* residual columns written                              */
 } rbo_info;
 
 /* ---- sparse-sign sketch (Section 3 / 5.2; the paper's Count sketch with zeta

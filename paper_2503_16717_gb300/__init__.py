@@ -59,7 +59,9 @@ class Info(C.Structure):
                 ("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
                 ("kernel_launches", C.c_int32), ("relres", C.c_double), ("est_relres", C.c_double),
                 ("time_ms", C.c_double), ("history", C.POINTER(C.c_double)),
-                ("history_cap", C.c_int32), ("history_len", C.c_int32)]
+                ("history_cap", C.c_int32), ("history_len", C.c_int32),
+                ("resid", C.c_void_p), ("resid_ld", C.c_int64), ("resid_cap", C.c_int32),
+                ("resid_len", C.c_int32)]
 
 
 class Csr(C.Structure):
@@ -166,7 +168,7 @@ def _vec(v, name: str):
 
 
 def info_dict(info: Info) -> dict:
-    d = {f: getattr(info, f) for f, _ in Info._fields_ if f not in ("history",)}
+    d = {f: getattr(info, f) for f, _ in Info._fields_ if f not in ("history", "resid")}
     d["breakdown_stage_name"] = STAGE_NAMES.get(info.breakdown_stage, "")
     return d
 
@@ -304,7 +306,7 @@ def mpk_csr(A: DeviceCSR, v0, s: int, V=None, dscale=None):
 def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int = 60,
                 tol: float = 1e-10, sk: Sketch | None = None, precision: int = PREC_FP64,
                 precond: int = 1, max_restarts: int = 0, history_cap: int = 4096,
-                M=None, raise_on_error: bool = False):
+                M=None, resid=None, raise_on_error: bool = False):
     """s-step GMRES(m); returns (x, info).  s_hat in (0, s] -> one-stage, else two-stage.
     ``M``: optional device tensor of preconditioner values on A's pattern (right
     preconditioner; overrides ``precond``)."""
@@ -316,6 +318,9 @@ def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int =
     info = Info()
     info.history = C.cast(hist, C.POINTER(C.c_double))
     info.history_cap = history_cap
+    if resid is not None:
+        pr, nrr, cap, ldr = _mat(resid, "resid")
+        info.resid, info.resid_ld, info.resid_cap = pr.value, ldr, cap
     o = _opts(precision, False, INTRA_RANDCHOLQR, max_restarts, precond)
     skh = sk.handle if sk is not None else None
     if M is not None:

@@ -124,9 +124,15 @@ static void info_clear(rbo_info* info) {
   if (!info) return;
   double* h = info->history;
   int32_t cap = info->history_cap;
+  double* rs = info->resid;
+  int64_t rld = info->resid_ld;
+  int32_t rcap = info->resid_cap;
   memset(info, 0, sizeof(*info));
   info->history = h;
   info->history_cap = cap;
+  info->resid = rs;
+  info->resid_ld = rld;
+  info->resid_cap = rcap;
   info->breakdown_block = -1;
   info->breakdown_column = -1;
 }

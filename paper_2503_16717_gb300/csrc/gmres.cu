@@ -155,6 +155,12 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   for (cycle = 0; cycle <= max_restarts; ++cycle) {
     // r = b - Ahat y into basis column 0, q0 = r / ||r||
     if ((e = residual_launch(Araw, b, x, w.Qb, ar->status, st))) return e;
+    if (info && info->resid && info->resid_len < info->resid_cap && info->resid_ld >= n) {
+      if ((e = note_cuda(cudaMemcpyAsync(info->resid + (int64_t)info->resid_len * info->resid_ld,
+                                         w.Qb, (size_t)n * 8, cudaMemcpyDeviceToDevice, st))))
+        return e;
+      info->resid_len++;
+    }
     c.launches += 1;
     if (cudaMemsetAsync(w.Rdev, 0, (size_t)ld * ld * 8, st) != cudaSuccess) return RBO_ERR_CUDA;
     if ((e = normalise_column(c, n, w.Qb, w.Rdev, ld, 0))) return e;
@@ -303,9 +309,15 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   if (info) {
     double* h = info->history;
     int32_t cap = info->history_cap;
+    double* rs = info->resid;
+    int64_t rld = info->resid_ld;
+    int32_t rcap = info->resid_cap;
     memset(info, 0, sizeof(*info));
     info->history = h;
     info->history_cap = cap;
+    info->resid = rs;
+    info->resid_ld = rld;
+    info->resid_cap = rcap;
     info->breakdown_block = -1;
     info->breakdown_column = -1;
   }

@@ -1,0 +1,144 @@
+"""GPU parity of the learned-SPAI network against the float64 oracle run with the
+same bfloat16-rounded weights: forward values of M, loss and gradient (the GPU
+keeps activations and sums in float32, so agreement is to float32 accuracy), the
+Jacobi special case, Adam descent, and GMRES with an SPAI right preconditioner."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gnn as ognn
+from oracle import krylov
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def problem():
+    A, meta = synth.convdiff2d_csr(24, seed=1001)
+    return A, ognn.Graph(A)
+
+
+def _theta(seed):
+    rng = np.random.default_rng(seed)
+    th = ognn.init_params(seed)
+    th[-97:] = rng.standard_normal(97) * 0.05          # non-trivial output layer
+    return th.astype(np.float32)
+
+
+def test_untrained_network_is_jacobi(rbo, problem):
+    A, G = problem
+    net = rbo.GNN(seed=3)
+    M = net.infer(rbo.DeviceCSR.from_host(A)).cpu().numpy()
+    expect = np.where(G.row == G.col, 1.0 / G.diag[G.row], 0.0)
+    assert np.array_equal(M, expect)
+
+
+def test_forward_matches_oracle(rbo, problem):
+    A, G = problem
+    th = _theta(7)
+    net = rbo.GNN(seed=0)
+    net.set_params(th)
+    M = net.infer(rbo.DeviceCSR.from_host(A)).cpu().numpy()
+    ref = ognn.forward(th.astype(np.float64), G, bf16=True)
+    assert np.abs(M - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+def test_loss_and_gradient_match_oracle(rbo, problem):
+    import torch
+    A, G = problem
+    th = _theta(11)
+    net = rbo.GNN(seed=0)
+    net.set_params(th)
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((A.n, 6))
+    Rd = rbo.colmajor(A.n, 6)
+    Rd.copy_(torch.from_numpy(R))
+    L, g = net.loss_grad(rbo.DeviceCSR.from_host(A), Rd)
+    Lr, gr = ognn.loss_and_grad(th.astype(np.float64), G, R, bf16=True)
+    assert abs(L - Lr) <= 1e-5 * abs(Lr)
+    assert np.linalg.norm(g - gr) <= 2e-3 * np.linalg.norm(gr)
+    # per parameter group (each weight matrix gets its own share of the signal)
+    o = 0
+    for name, shp in ognn.param_shapes():
+        k = int(np.prod(shp))
+        ng = np.linalg.norm(gr[o:o + k])
+        if ng > 1e-8 * np.linalg.norm(gr):
+            assert np.linalg.norm(g[o:o + k] - gr[o:o + k]) <= 5e-3 * ng, name
+        o += k
+
+
+def test_adam_training_reduces_loss(rbo, problem):
+    import torch
+    A, G = problem
+    Ad = rbo.DeviceCSR.from_host(A)
+    net = rbo.GNN(seed=1)
+    R = rbo.colmajor(A.n, 8)
+    R.copy_(torch.from_numpy(np.random.default_rng(9).standard_normal((A.n, 8))))
+    losses = [net.train_step(Ad, R, lr=3e-3) for _ in range(60)]
+    assert losses[-1] < 0.8 * losses[0]
+    # the oracle's Adam from the same start takes the same first step
+    th0 = rbo.GNN(seed=1).get_params()
+    net2 = rbo.GNN(seed=1)
+    l0 = net2.train_step(Ad, R, lr=3e-3)
+    L, g = ognn.loss_and_grad(th0.astype(np.float64), G, R.cpu().numpy(), bf16=True)
+    t1, _, _ = ognn.adam_step(th0.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr=3e-3)
+    moved = np.abs(g) > 1e-3 * np.abs(g).max()
+    assert np.allclose(net2.get_params()[moved], t1[moved], atol=3e-6)
+
+
+def test_gmres_with_spai_beats_jacobi(rbo):
+    import torch
+    A, _ = synth.convdiff2d_csr(48, seed=1002)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    bd = torch.from_numpy(b).cuda()
+    Ms = ognn.spai(A)
+    xs, i_spai = rbo.sstep_gmres(Ad, bd, s=5, m=30, tol=1e-10, M=torch.from_numpy(Ms).cuda())
+    xj, i_jac = rbo.sstep_gmres(Ad, bd, s=5, m=30, tol=1e-10)
+    assert i_spai["converged"] == 1 and i_jac["converged"] == 1
+    assert i_spai["iterations"] < i_jac["iterations"]
+    r = b - A.to_scipy() @ xs.cpu().numpy()
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    # the oracle's s-step GMRES with the same right preconditioner agrees on the count
+    import scipy.sparse as sp
+    Mop = sp.csr_matrix((Ms, A.col, A.rowptr), shape=(A.n, A.n))
+    AM = synth.CSR.from_scipy(A.to_scipy() @ Mop)
+    ref = krylov.sstep_gmres(AM, b, s=5, m=30, tol=1e-10, precond="none")
+    assert abs(ref.iterations - i_spai["iterations"]) <= 5
+
+
+def test_structurally_unsymmetric_pattern_rejected(rbo):
+    import scipy.sparse as sp
+    A = sp.csr_matrix(np.array([[2.0, 1.0, 0.0], [0.0, 2.0, 0.0], [0.0, 1.0, 2.0]]))
+    net = rbo.GNN(seed=0)
+    with pytest.raises(rbo.RboError) as e:
+        net.infer(rbo.DeviceCSR.from_host(synth.CSR.from_scipy(A)))
+    assert e.value.code == rbo.ERR_ARG
+
+
+def test_trained_network_gains_over_jacobi(rbo):
+    """Train on generated convection-diffusion instances (residuals from Jacobi
+    s-step GMRES), evaluate on unseen, larger instances: the learned M must lower
+    the probe loss below Jacobi's and must not need more GMRES iterations (the
+    Jacobi fallback guards the iteration count); the gain is printed."""
+    import torch
+    from paper_2503_16717_gb300 import learned
+    gen = synth.convdiff2d_csr
+    train_set = learned.make_instances(lambda N, sd: gen(N, sd, corr=8.0), range(3000, 3024), 48)
+    net = rbo.GNN(seed=2)
+    hist = learned.train(net, train_set, epochs=6, lr=3e-3)
+    assert hist["epoch_loss"][-1] < hist["epoch_loss"][0]
+    jac = rbo.GNN(seed=0)
+    its_l, its_j = [], []
+    for sd in (4000, 4001, 4002):
+        Ah, _ = gen(96, sd, corr=8.0)
+        A = rbo.DeviceCSR.from_host(Ah)
+        b = torch.from_numpy(synth.ones_rhs(Ah)).cuda()
+        x, info, used = learned.solve(net, A, b, jacobi=jac, s=5, m=30, tol=1e-10)
+        _, ij = rbo.sstep_gmres(A, b, s=5, m=30, tol=1e-10)
+        assert info["converged"] == 1 and ij["converged"] == 1
+        its_l.append(info["iterations"])
+        its_j.append(ij["iterations"])
+        assert info["learned_loss"] < info["jacobi_loss"]
+    print("learned vs jacobi iterations:", its_l, its_j, "epoch loss:", hist["epoch_loss"])
+    assert np.mean(its_l) <= np.mean(its_j)
