@@ -159,6 +159,31 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     sec_per_solve = ms_per_step / 2.0 / 1e3
 
+    # the same solves in float32-pair arithmetic (RBO_PREC_DF64)
+    df64 = None
+    if not args.no_df64:
+        def solve_df(s_hat):
+            x.zero_()
+            _, info = rbo.sstep_gmres(Ad, bd, x, s=S, s_hat=s_hat, m=M, tol=TOL,
+                                      precision=rbo.PREC_DF64)
+            if info["status"] != 0:
+                raise RuntimeError(f"sstep_gmres df64 failed: {info}")
+            return info
+        solve_df(0)
+        solve_df(S_HAT)
+        barrier()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record()
+        for _ in range(args.steps):
+            i1 = solve_df(0)
+            i2 = solve_df(S_HAT)
+        d1.record()
+        barrier()
+        dms = d0.elapsed_time(d1) / args.steps
+        df64 = {"s_per_solve": dms / 2.0 / 1e3, "ms_per_step": dms,
+                "one_stage": {"iterations": i1["iterations"], "relres": i1["relres"]},
+                "two_stage": {"iterations": i2["iterations"], "relres": i2["relres"]}}
+
     # per-kernel times with CUDA events around each library launch (same steps again)
     if args.no_prof:
         prof, roofline, ms_prof = None, None, None
@@ -169,6 +194,7 @@ def run_ours(args):
     e2e = None if args.no_e2e else run_e2e(rbo, torch, A, b_host, args)
 
     orth = run_orth(rbo, torch, args) if (rank == 0 and not args.no_orth) else None
+    learned_res = run_learned(rbo, torch, args) if (rank == 0 and not args.no_learned) else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(A, b_host, last["one"]["iterations"])
@@ -189,6 +215,7 @@ def run_ours(args):
                 "two_stage": {"iterations": two["iterations"], "restarts": two["restarts"],
                               "relres": two["relres"], "kernel_launches": two["kernel_launches"]},
             },
+            "df64": df64,
             "ms_per_step_profiled": ms_prof,
             "kernels": prof,
             "roofline": roofline,
@@ -196,6 +223,7 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "clocks": clk.summary(),
             "orth": orth,
+            "learned": learned_res,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -216,6 +244,19 @@ def profile_steps(rbo, torch, step, barrier, args):
     ms_prof = e0.elapsed_time(e1) / args.steps
     prof = {k: rbo.profile_read(v) for k, v in
             (("rowpass", rbo.PROF_ROWPASS), ("spmv", rbo.PROF_SPMV), ("vector", rbo.PROF_VECTOR))}
+    names = {1: "P1_gram", 2: "P2_update_sketch", 3: "P3_trsm_gram", 4: "P4_trsm_gram2",
+             5: "P5_reorth_update_gram", 6: "P6_trsm", 7: "T1_gram", 8: "T2_update_sketch",
+             9: "T3_forward_subst_gram", 10: "T4_trsm_gram2", 11: "T5_reorth_update_gram",
+             12: "T6_trsm", 13: "normalise", 0: "other"}
+    passes = {}
+    for tag, nm in names.items():
+        r = rbo.profile_read(8 + tag)
+        if r["launches"]:
+            r["share_of_rowpass"] = r["ms"] / max(prof["rowpass"]["ms"], 1e-9)
+            r["tflops"] = r["flops"] / (r["ms"] / 1e3) / 1e12 if r["ms"] > 0 else 0.0
+            r["gbs"] = r["bytes"] / (r["ms"] / 1e3) / 1e9 if r["ms"] > 0 else 0.0
+            passes[nm] = r
+    prof["rowpass_by_role"] = passes
     rbo.profile_enable(False)
     rp = prof["rowpass"]
     avg_ms = rp["ms"] / max(rp["launches"], 1)
@@ -284,7 +325,7 @@ def run_orth(rbo, torch, args):
             torch.cuda.empty_cache()
             V0 = synth.glued_blocks_torch(n, nb, s, kappa, seed=1, v0=True, device="cuda")
         for scheme in ("two", "one"):
-            for prec in (rbo.PREC_FP64, rbo.PREC_MIXED):
+            for prec in (rbo.PREC_FP64, rbo.PREC_MIXED, rbo.PREC_DF64):
                 Wm = W.t()  # n x c column-major view
                 times = []
                 info = None
@@ -320,13 +361,87 @@ def run_orth(rbo, torch, args):
                         passes += (P + 2 * s_hat) + (P + 2 * s_hat) + 2 * s_hat
                 gb = passes * 8.0 * n / 1e9
                 out.append({"kappa": kappa, "scheme": scheme,
-                            "precision": "fp64" if prec == rbo.PREC_FP64 else "mixed",
+                            "precision": {rbo.PREC_FP64: "fp64", rbo.PREC_MIXED: "mixed",
+                                          rbo.PREC_DF64: "df64"}[prec],
                             "status": info["status"], "ms": ms, "cols_per_s": c / (ms / 1e3),
                             "hbm_gbs_algorithmic": gb / (ms / 1e3), "orth_err": oe,
                             "launches": info["kernel_launches"]})
     del V0, W
     torch.cuda.empty_cache()
     return {"n": n, "cols": c, "s": s, "s_hat": s_hat, "d": 4 * c, "results": out}
+
+
+def run_learned(rbo, torch, args):
+    """Learned SPAI preconditioner on the convection-diffusion family (config 3 shape,
+    reduced sizes by default): train on generated instances with residuals from
+    Jacobi s-step GMRES, evaluate s-step GMRES(m=60, s=5, s_hat=30) to 1e-10 on
+    unseen instances against Jacobi.  --learned-full runs the full sizes
+    (256 training instances at 512^2, 32 evaluation instances at 2048^2)."""
+    import numpy as np
+    import synth
+    from paper_2503_16717_gb300 import learned
+    full = args.learned_full
+    n_train, N_train = (256, 512) if full else (32, 128)
+    n_eval, N_eval = (32, 2048) if full else (2, 512)
+    t0 = time.perf_counter()
+    train_set = learned.make_instances(synth.convdiff2d_csr, range(3000, 3000 + n_train), N_train)
+    t_gen = time.perf_counter() - t0
+    net = rbo.GNN(seed=2)
+    hist = learned.train(net, train_set, epochs=8, lr=3e-3, lr_decay=0.8)
+    jac = rbo.GNN(seed=0)
+    # kernel timing: one training step and one inference
+    A0 = train_set[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        net.loss_grad(A0.A, A0.R)
+    e1.record()
+    torch.cuda.synchronize()
+    grad_ms = e0.elapsed_time(e1) / 5
+    del train_set
+    rows = []
+    infer_ms = None
+    for sd in range(4000, 4000 + n_eval):
+        Ah, meta = synth.convdiff2d_csr(N_eval, sd)
+        A = rbo.DeviceCSR.from_host(Ah)
+        b = torch.from_numpy(synth.ones_rhs(Ah)).cuda()
+        if infer_ms is None:
+            net.infer(A)
+            torch.cuda.synchronize()
+            e0.record()
+            net.infer(A)
+            e1.record()
+            torch.cuda.synchronize()
+            infer_ms = e0.elapsed_time(e1)
+            nnz_eval = A.nnz
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        x, info, used = learned.solve(net, A, b, jacobi=jac, s=5, s_hat=30, m=60, tol=1e-10)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        _, ij = rbo.sstep_gmres(A, b, s=5, s_hat=30, m=60, tol=1e-10)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        rows.append({"seed": sd, "peclet": meta["peclet"], "learned_used": bool(used),
+                     "iters_learned": info["iterations"], "iters_jacobi": ij["iterations"],
+                     "relres_learned": info["relres"], "relres_jacobi": ij["relres"],
+                     "s_learned": t2 - t1, "s_jacobi": t3 - t2,
+                     "loss_learned": info["learned_loss"], "loss_jacobi": info["jacobi_loss"]})
+        del A, b, x
+    il = float(np.mean([r["iters_learned"] for r in rows]))
+    ij_ = float(np.mean([r["iters_jacobi"] for r in rows]))
+    # forward traffic per edge: per layer e (r/w), m (w), h_j gather (r), plus encoders/decoder
+    bytes_infer = nnz_eval * (3 * 4 * 128 + 3 * 128 + 12 + 8)
+    return {"train": {"instances": n_train, "grid": N_train, "epochs": 8,
+                      "epoch_loss": hist["epoch_loss"], "train_s": hist["seconds"],
+                      "generate_s": t_gen, "loss_grad_ms": grad_ms},
+            "eval": {"instances": n_eval, "grid": N_eval, "mean_iters_learned": il,
+                     "mean_iters_jacobi": ij_, "iteration_ratio": il / ij_,
+                     "mean_s_learned": float(np.mean([r["s_learned"] for r in rows])),
+                     "mean_s_jacobi": float(np.mean([r["s_jacobi"] for r in rows])),
+                     "rows": rows},
+            "infer_ms": infer_ms, "infer_edges": nnz_eval,
+            "infer_gbs_algorithmic": bytes_infer / (infer_ms / 1e3) / 1e9 if infer_ms else None}
 
 
 # ------------------------------------------------------------------------------------------
@@ -400,6 +515,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-prof", action="store_true")
+    ap.add_argument("--no-df64", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-full", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -57,6 +57,14 @@ extern "C" {
                               float32 with float32 accumulation; Gram matrices feeding
                               the final Cholesky, the small factors, every update of V
                               and the final TRSM in float64                             */
+#define RBO_PREC_DF64   2  /* float64 data; every Gram matrix and the re-orthogonalization
+                              update (whose coefficients are O(eps kappa)) in float32
+                              pairs (about 48 significant bits, error-free
+                              transformations on the FP32 pipe, Gram sums flushed to
+                              float64 every ~64 terms); first-pass projections, TRSMs,
+                              the sketch and the small factors in float64.  Only steps
+                              that cannot reach the backward error ||V - QR|| are
+                              moved off the float64 pipe                              */
 
 /* ---- intra-block choice (one-stage) ----------------------------------------- */
 #define RBO_INTRA_RANDCHOLQR 0  /* RandCholQR (Figure 4b)                                */
@@ -272,6 +280,11 @@ int rbo_gnn_train_step(rbo_gnn g, const rbo_csr* A, const double* R, int32_t nr,
 #define RBO_PROF_ROWPASS 0  /* the fused tall-skinny row pass (Gram / update / TRSM / sketch) */
 #define RBO_PROF_SPMV    1  /* CSR SpMV of the matrix-powers kernel and residuals           */
 #define RBO_PROF_VECTOR  2  /* small vector kernels (Jacobi setup, x update, scaling)       */
+/* Row passes are also accumulated by role under kind RBO_PROF_PASS + role:
+ * 1..6 one-stage P1 (Gram C1), P2 (update + sketch), P3 (TRSM R_hat + Gram),
+ * P4 (TRSM R' + Gram C2), P5 (re-orthogonalization update + Gram), P6 (final TRSM);
+ * 7..12 two-stage T1..T6 (same roles per big panel); 13 normalisations; 0 other.   */
+#define RBO_PROF_PASS    8
 int rbo_profile_enable(int on);
 int rbo_profile_reset(void);
 int rbo_profile_read(int32_t kind, int64_t* launches, double* ms, double* bytes, double* flops);

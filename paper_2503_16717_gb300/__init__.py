@@ -43,6 +43,7 @@ ERR_NO_DEVICE = -8
 ERR_LOST_ORTHOGONALITY = -9
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_DF64 = 2
 INTRA_RANDCHOLQR = 0
 INTRA_CHOLQR2 = 1
 STAGE_NAMES = {0: "", 1: "v0", 2: "intra", 3: "intra2", 4: "final", 5: "bigpanel"}

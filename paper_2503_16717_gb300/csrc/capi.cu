@@ -272,7 +272,8 @@ static int orth_common_checks(int64_t n, int32_t ncols, int32_t s, double* V, in
     return RBO_ERR_ARG;
   if (n < ncols) return RBO_ERR_ARG;
   if ((ncols - v0) % s != 0) return RBO_ERR_ARG;
-  if (opts && (opts->precision != RBO_PREC_FP64 && opts->precision != RBO_PREC_MIXED))
+  if (opts && (opts->precision != RBO_PREC_FP64 && opts->precision != RBO_PREC_MIXED &&
+               opts->precision != RBO_PREC_DF64))
     return RBO_ERR_ARG;
   return RBO_OK;
 }
@@ -324,6 +325,7 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   c.ar = ar;
   c.st = st;
   c.mixed = (opts && opts->precision == RBO_PREC_MIXED) ? 1 : 0;
+  c.df64 = (opts && opts->precision == RBO_PREC_DF64) ? 1 : 0;
   if (rand) {
     c.d = sk->d;
     c.zeta = sk->zeta;

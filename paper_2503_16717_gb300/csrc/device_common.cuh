@@ -163,3 +163,113 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
 }
 
 }  // namespace rbo
+
+namespace rbo {
+// ---- float32-pair ("df64") arithmetic on the FP32 pipe -------------------------------
+// A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)), about 48
+// significant bits.  Error-free transformations: TwoSum (Knuth) and the FMA-based
+// TwoProduct (Dekker's product with a fused multiply-add); see Joldes, Muller and
+// Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic", ACM TOMS 2017.
+struct df {
+  float h, l;
+};
+
+// float64 -> float pair with integer operations only: hi = the leading 24 bits
+// (truncated), lo = the next 29 bits rounded to a float.  Values below 2^-74 in
+// magnitude keep only hi (relative error 2^-24), values below the float32 normal
+// range flush to zero.
+__device__ __forceinline__ df df_from_double(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const unsigned sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7FF);   // biased float64 exponent
+  const int ef = e - 1023 + 127;
+  df r;
+  if (ef <= 0 || e == 0x7FF) {
+    if (e == 0x7FF) {  // inf / nan: propagate in hi
+      r.h = __uint_as_float(sign | 0x7F800000u | (((hi32 & 0xFFFFFu) | lo32) ? 0x400000u : 0u));
+    } else {
+      r.h = 0.0f;
+    }
+    r.l = 0.0f;
+    return r;
+  }
+  if (ef >= 255) {
+    r.h = __uint_as_float(sign | 0x7F800000u);
+    r.l = 0.0f;
+    return r;
+  }
+  const unsigned mant23 = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+  r.h = __uint_as_float(sign | ((unsigned)ef << 23) | mant23);
+  const unsigned rem = lo32 & 0x1FFFFFFFu;  // the 29 mantissa bits below hi
+  // lo = rem * 2^(e - 1023 - 52): the float 2^(e-1023-52) has biased exponent ef - 52
+  const int el = ef - 52;
+  if (rem == 0u || el < 1) {
+    r.l = 0.0f;
+  } else {
+    const float lo = __uint2float_rn(rem) * __uint_as_float((unsigned)el << 23);
+    r.l = sign ? -lo : lo;
+  }
+  return r;
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  df r;
+  r.h = a + b;
+  r.l = b - (r.h - a);
+  return r;
+}
+
+// acc += x * y  (all float pairs), accumulator not renormalised (l absorbs the errors)
+__device__ __forceinline__ void df_fma_acc(df& acc, df x, df y) {
+  const float p = x.h * y.h;
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  const float s = acc.h + p;
+  const float bb = s - acc.h;
+  const float err = (acc.h - (s - bb)) + (p - bb);
+  acc.l += err + e;
+  acc.h = s;
+}
+
+// acc += v (v a float pair)
+__device__ __forceinline__ void df_add_acc(df& acc, df v) {
+  const float s = acc.h + v.h;
+  const float bb = s - acc.h;
+  const float err = (acc.h - (s - bb)) + (v.h - bb);
+  acc.l += err + v.l;
+  acc.h = s;
+}
+
+__device__ __forceinline__ df df_norm(df a) { return df_fast_two_sum(a.h, a.l); }
+
+// a * b (renormalised)
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.h, -a.l}; }
+}  // namespace rbo
+
+namespace rbo {
+// float -> double by integer operations (exact; float subnormals flush to zero)
+__device__ __forceinline__ double f32_to_f64_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  if (e == 0xFFu) return __hiloint2double((int)(sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u)), 0);
+  return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+// float pair -> double (one float64 addition)
+__device__ __forceinline__ double df_to_double_fast(df a) {
+  return f32_to_f64_int(a.h) + f32_to_f64_int(a.l);
+}
+}  // namespace rbo

@@ -101,6 +101,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   c.ar = ar;
   c.st = st;
   c.mixed = (opts && opts->precision == RBO_PREC_MIXED) ? 1 : 0;
+  c.df64 = (opts && opts->precision == RBO_PREC_DF64) ? 1 : 0;
   c.d = d;
   c.zeta = zeta;
   c.seed = seed;
@@ -332,7 +333,8 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   if (code == RBO_OK && A->n < m + 1) code = RBO_ERR_ARG;
   if (code == RBO_OK && (int64_t)(sk ? sk->d : 4 * (m + 1)) * s > MAX_SKETCH_DK) code = RBO_ERR_ARG;
   if (code == RBO_OK && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
-  if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 && opts->precision != RBO_PREC_MIXED)
+  if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 &&
+      opts->precision != RBO_PREC_MIXED && opts->precision != RBO_PREC_DF64)
     code = RBO_ERR_ARG;
   int d = 4 * (m + 1), zeta = 8;
   uint64_t seed = 42;

@@ -13,7 +13,7 @@ namespace rbo {
 namespace {
 struct Rec {
   cudaEvent_t a, b;
-  int kind;
+  int kind, tag;
   double bytes, flops;
 };
 std::mutex mu;
@@ -46,12 +46,12 @@ ProfToken prof_start(cudaStream_t st) {
   return t;
 }
 
-void prof_stop(const ProfToken& t, cudaStream_t st, int kind, double b, double f) {
+void prof_stop(const ProfToken& t, cudaStream_t st, int kind, double b, double f, int tag) {
   if (!enabled || t.ev == nullptr) return;
   std::lock_guard<std::mutex> lk(mu);
   cudaEvent_t e2 = get_event();
   cudaEventRecord(e2, st);
-  pending.push_back(Rec{(cudaEvent_t)t.ev, e2, kind, b, f});
+  pending.push_back(Rec{(cudaEvent_t)t.ev, e2, kind, tag, b, f});
 }
 
 void prof_drain() {
@@ -59,10 +59,13 @@ void prof_drain() {
   for (auto& r : pending) {
     float t = 0.f;
     if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
-      cnt[r.kind] += 1;
-      ms[r.kind] += t;
-      bytes[r.kind] += r.bytes;
-      flops[r.kind] += r.flops;
+      for (int k : {r.kind, r.tag >= 0 ? 8 + r.tag : -1}) {
+        if (k < 0 || k >= PROF_KINDS) continue;
+        cnt[k] += 1;
+        ms[k] += t;
+        bytes[k] += r.bytes;
+        flops[k] += r.flops;
+      }
     }
     pool.push_back(r.a);
     pool.push_back(r.b);

@@ -130,7 +130,10 @@ struct RowPass {
   int acc_y = 0;                 // accumulate Y'^T Y'
   int sk_d = 0, sk_zeta = 0; uint64_t sk_seed = 0;  // accumulate S Y' (d x b)
   int mixed = 0;                 // float32 accumulation of X^T Y' and S Y'
+  int df64 = 0;                  // float32-pair arithmetic for the Gram (and small projections)
+  int small_coeffs = 0;          // C is a re-orthogonalization (O(eps kappa)) coefficient block
   int max_ctas = 0;              // cap on the grid (0: none); bounds the reduction scratch
+  int tag = 0;                   // role for the per-kernel timing (RBO_PROF_PASS_*)
   Epilogue epi;
 };
 
@@ -175,6 +178,7 @@ struct OrthCtx {
   cudaStream_t st = nullptr;
   int launches = 0;
   int mixed = 0;
+  int df64 = 0;   // every pass in float32-pair arithmetic where it applies
   int d = 0, zeta = 0; uint64_t seed = 0;
   // small device buffers, sized once per call by orth_ctx_alloc and reused by every
   // block (stream order makes the reuse safe)
@@ -223,13 +227,15 @@ int finish_status(Arena* ar, cudaStream_t st, rbo_info* info);
 int note_cuda(cudaError_t e);
 
 // ---- optional per-kernel timing (rbo_profile_*) ----------------------------------------
-constexpr int PROF_KINDS = 4;  // RBO_PROF_ROWPASS, _SPMV, _VECTOR, _SKETCH_ENTRIES
+// kinds 0..7: RBO_PROF_*; 8 + tag: row passes by role (RowPass::tag)
+constexpr int PROF_KINDS = 32;
 struct ProfToken {
   void* ev = nullptr;
 };
 bool prof_on();
 ProfToken prof_start(cudaStream_t st);
-void prof_stop(const ProfToken& t, cudaStream_t st, int kind, double bytes, double flops);
+void prof_stop(const ProfToken& t, cudaStream_t st, int kind, double bytes, double flops,
+               int tag = -1);
 void prof_drain();
 
 }  // namespace rbo

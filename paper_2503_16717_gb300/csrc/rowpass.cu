@@ -37,6 +37,7 @@ struct PassDev {
   int TP;             // shared-memory column stride of a tile (T + 2: fewer bank conflicts)
   int ntiles;
   int items, tpo, tasks;  // Z work split: items = zr * ceil(b / CB), tpo row subsets
+  int flush_tiles;        // float-pair Gram: tiles between flushes into float64
   int use_bulk;       // X/Y aligned for 16-byte bulk copies
   int zr, no;         // Z rows, Z outputs (zr * b)
   int L;              // partial length (no + d*b)
@@ -260,8 +261,13 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
 // ------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------
-template <bool MIXED>
+template <int ARITH>
 __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ PassDev P) {
+  // ARITH 0: float64; 1: float32 for X^T Y' and the sketch (mixed precision);
+  // 2: float32 pairs for the transform and the Gram, float64 for the sketch
+  constexpr bool MIXED = ARITH == 1;
+  constexpr bool DF = ARITH == 2;
+  constexpr int IPTA = DF ? 2 : IPT;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_flag;
   __shared__ int s_last;
@@ -285,7 +291,13 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
   // small matrices + sketch copies
   if (rp.C) {
     const int ldc = rp.ldc > 0 ? rp.ldc : a;
-    for (int t = tid; t < a * b; t += NT) Cs[t] = rp.C[(t % a) + (size_t)(t / a) * ldc];
+    for (int t = tid; t < a * b; t += NT) {
+      const double v = rp.C[(t % a) + (size_t)(t / a) * ldc];
+      if (DF && rp.small_coeffs && !rp.Tri)
+        reinterpret_cast<df*>(Cs)[t] = df_from_double(v);
+      else
+        Cs[t] = v;
+    }
   }
   if (rp.Tri) {
     const int ldt = rp.ldtri > 0 ? rp.ldtri : b;
@@ -310,15 +322,33 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
 
   // Z tasks: item = (Z row i, block of up to CB columns), split over `tpo` row
   // subsets; thread t owns tasks t, t + NT, ... (at most IPT)
-  double acc[IPT][CB];
-  float accf[IPT][CB];
+  double acc[IPTA][CB];
+  float accf[IPTA][CB];
+  df acci[IPTA][CB];  // float-pair partial sums, flushed into acc every few tiles
 #pragma unroll
-  for (int k = 0; k < IPT; ++k)
+  for (int k = 0; k < IPTA; ++k)
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
       acc[k][c] = 0.0;
       accf[k][c] = 0.0f;
+      acci[k][c] = df{0.f, 0.f};
     }
+  int since_flush = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < IPTA; ++k)
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        acc[k][c] += df_to_double_fast(acci[k][c]);
+        acci[k][c] = df{0.f, 0.f};
+      }
+  };
+  // float-pair arithmetic: the projection only when its coefficients are small
+  // (re-orthogonalization, whose subtrahend is O(eps kappa) of the data), so that the
+  // 48-bit rounding cannot reach the backward error; triangular solves and
+  // large-coefficient projections stay float64; Gram sums always in pairs
+  const bool df_pre = DF && !rp.Tri && rp.C && rp.small_coeffs;
+  const bool df_post = DF && P.no > 0 && !df_pre;
 
   const int ncol_tile = (a + b);
   auto stage_X = [&](int s) {
@@ -380,6 +410,16 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
       issue_tile(nxt, s ^ 1);
     }
 
+    // float64 -> float pairs in place (8 bytes each), integer operations only
+    auto to_pairs = [&]() {
+      for (int t = tid; t < ncol_tile * T; t += NT) {
+        const size_t e = (size_t)(t / T) * TP + (t % T);
+        reinterpret_cast<df*>(xs)[e] = df_from_double(xs[e]);
+      }
+      __syncthreads();
+    };
+    if (df_pre) to_pairs();
+
     // sketch entries of the tile's rows (integer hash; -1 marks rows past n)
     if (do_sk) {
       for (int r = tid; r < T; r += NT) {
@@ -406,6 +446,19 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
       }
     };
     auto project = [&]() {
+      if (df_pre) {
+        df* yp = reinterpret_cast<df*>(ys);
+        const df* xp = reinterpret_cast<const df*>(xs);
+        const df* cp = reinterpret_cast<const df*>(Cs);
+        for (int t = tid; t < T * b; t += NT) {
+          const int r = t % T, c = t / T;
+          const df* cc = cp + (size_t)c * a;
+          df v = yp[c * TP + r];
+          for (int i = 0; i < a; ++i) df_fma_acc(v, df_neg(xp[i * TP + r]), cc[i]);
+          yp[c * TP + r] = df_norm(v);
+        }
+        return;
+      }
       // one (row, column) element per task; two interleaved partial sums
       for (int t = tid; t < T * b; t += NT) {
         const int r = t % T, c = t / T;
@@ -435,8 +488,18 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
     if (rp.write_y) {
       for (int t = tid; t < b * T; t += NT) {
         int c = t / T, rr = t % T;
-        if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = ys[(size_t)c * TP + rr];
+        if (df_pre) {
+          const size_t e = (size_t)c * TP + rr;
+          const double v = df_to_double_fast(reinterpret_cast<const df*>(ys)[e]);
+          if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = v;
+        } else {
+          if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = ys[(size_t)c * TP + rr];
+        }
       }
+    }
+    if (df_post) {
+      __syncthreads();  // float64 values of the tile consumed by the write-back
+      to_pairs();
     }
 
     // ---- phase B: Gram outputs Z = [X, Y']^T Y' --------------------------------
@@ -451,9 +514,32 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
       }
       __syncthreads();
     }
-    if (P.no > 0) {
+    if (DF && P.no > 0) {
 #pragma unroll
-      for (int k = 0; k < IPT; ++k) {
+      for (int k = 0; k < IPTA; ++k) {
+        const int task = tid + k * NT;
+        if (task < P.tasks) {
+          const int item = task % P.items, g = task / P.items;
+          const int i = item % P.zr, c0 = (item / P.zr) * CB;
+          const int cw = min(CB, b - c0);
+          const df* zsrc = reinterpret_cast<const df*>((i < ax) ? xs + (size_t)i * TP
+                                                                 : ys + (size_t)(i - ax) * TP);
+          const df* ysrc = reinterpret_cast<const df*>(ys + (size_t)c0 * TP);
+          for (int rr = g; rr < T; rr += P.tpo) {
+            const df z = zsrc[rr];
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+              if (c < cw) df_fma_acc(acci[k][c], z, ysrc[(size_t)c * TP + rr]);
+          }
+        }
+      }
+      if (++since_flush >= P.flush_tiles) {
+        flush();
+        since_flush = 0;
+      }
+    } else if (P.no > 0) {
+#pragma unroll
+      for (int k = 0; k < IPTA; ++k) {
         const int task = tid + k * NT;
         if (task < P.tasks) {
           const int item = task % P.items, g = task / P.items;
@@ -529,10 +615,11 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
   if (P.L == 0) return;
   double* mypart = P.partials + (size_t)blockIdx.x * P.L;
   if (P.no > 0) {
+    if (DF) flush();
     // combine the tpo row-subset partial sums of every item in a fixed order
     double* comb = reinterpret_cast<double*>(smem + P.off_stage);  // tasks x CB
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) {
+    for (int k = 0; k < IPTA; ++k) {
       const int task = tid + k * NT;
       if (task < P.tasks)
 #pragma unroll
@@ -613,22 +700,22 @@ static int sm_count() {
   return g_num_sms;
 }
 
-static int g_smem_max[2] = {0, 0};
+static int g_smem_max[3] = {0, 0, 0};
 
 // Largest dynamic shared memory of the row-pass kernel (opt-in limit minus its
 // static shared memory); raises the kernel's limit to it on first use.
-template <bool MIXED>
+template <int ARITH>
 static int smem_limit() {
-  int& lim = g_smem_max[MIXED ? 1 : 0];
+  int& lim = g_smem_max[ARITH];
   if (lim == 0) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     size_t stat = 0;
-    if (cudaFuncGetAttributes(&fa, rowpass_kernel<MIXED>) == cudaSuccess) stat = fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, rowpass_kernel<ARITH>) == cudaSuccess) stat = fa.sharedSizeBytes;
     lim = optin - (int)stat - 64;
-    if (cudaFuncSetAttribute(rowpass_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(rowpass_kernel<ARITH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              lim) != cudaSuccess) {
       cudaGetLastError();
       lim = 48 * 1024 - (int)stat;
@@ -637,14 +724,14 @@ static int smem_limit() {
   return lim;
 }
 
-template <bool MIXED>
+template <int ARITH>
 static int occupancy(int smem) {
-  long long key = (long long)smem * 2 + (MIXED ? 1 : 0);
+  long long key = (long long)smem * 4 + ARITH;
   auto it = g_occ.find(key);
   if (it != g_occ.end()) return it->second;
   int nb = 0;
-  smem_limit<MIXED>();
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<MIXED>, NT, smem) !=
+  smem_limit<ARITH>();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<ARITH>, NT, smem) !=
       cudaSuccess) {
     cudaGetLastError();
     nb = 1;
@@ -681,10 +768,18 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   if (no > 8192) return RBO_ERR_ARG;
   const int dsk = rp.sk_d > 0 ? rp.sk_d : 0;
   const int L = no + dsk * rp.b;
-  const int mixed = rp.mixed ? 1 : 0;
   // Z work split: items (Z row, block of CB columns), tpo row subsets per item
   const int items = zr * ((rp.b + CB - 1) / CB);
   if (items > IPT * NT) return RBO_ERR_ARG;
+  // arithmetic: float32 pairs only where they apply (transform or Gram, no sketch
+  // together with a Gram, at most 2 Gram tasks per thread); float64 otherwise
+  int arith = rp.mixed ? 1 : 0;
+  if (rp.df64 && !rp.mixed) {
+    const bool pre = !rp.Tri && rp.C && rp.small_coeffs;
+    const bool ok = (no > 0 || pre) && dsk == 0 && items <= 2 * NT;
+    arith = ok ? 2 : 0;
+  }
+  const int mixed = arith == 1 ? 1 : 0;
 
   // choose the tile height: largest of 64/32/16 that fits
   int T = 64;
@@ -723,10 +818,11 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     if (smem <= 220 * 1024 || T == 16) break;
     T /= 2;
   }
-  const int limit = mixed ? smem_limit<true>() : smem_limit<false>();
+  const int limit = arith == 1 ? smem_limit<1>() : (arith == 2 ? smem_limit<2>() : smem_limit<0>());
   if ((long long)smem > limit) return RBO_ERR_ARG;
   const int ntiles = (int)((rp.n + T - 1) / T);
-  const int occ = mixed ? occupancy<true>((int)smem) : occupancy<false>((int)smem);
+  const int occ = arith == 1 ? occupancy<1>((int)smem)
+                             : (arith == 2 ? occupancy<2>((int)smem) : occupancy<0>((int)smem));
   int G = std::min(ntiles, occ * sm_count());
   if (rp.max_ctas > 0) G = std::min(G, rp.max_ctas);
   if (G < 1) G = 1;
@@ -740,6 +836,8 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.items = items;
   P.tpo = tpo;
   P.tasks = tasks;
+  // float-pair Gram chains are flushed into float64 after about 64 products
+  P.flush_tiles = std::max(1, 64 / std::max(1, T / tpo));
   const bool alignedX = rp.a == 0 || (((uintptr_t)rp.X & 15) == 0 && (rp.ldx % 2) == 0);
   const bool alignedY = (((uintptr_t)rp.Y & 15) == 0 && (rp.ldy % 2) == 0);
   P.use_bulk = (alignedX && alignedY) ? 1 : 0;
@@ -771,10 +869,12 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     P.tickets = ar->tickets;
   }
   ProfToken tok = prof_start(st);
-  if (mixed)
-    rowpass_kernel<true><<<G, NT, smem, st>>>(P);
+  if (arith == 1)
+    rowpass_kernel<1><<<G, NT, smem, st>>>(P);
+  else if (arith == 2)
+    rowpass_kernel<2><<<G, NT, smem, st>>>(P);
   else
-    rowpass_kernel<false><<<G, NT, smem, st>>>(P);
+    rowpass_kernel<0><<<G, NT, smem, st>>>(P);
   if (prof_on()) {
     // algorithmic traffic: every n-row column read once, written once
     const double nn = (double)rp.n, A = rp.a, B = rp.b;
@@ -786,7 +886,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     if (rp.acc_x) fl += 2.0 * nn * A * B;                     // X^T Y'
     if (rp.acc_y) fl += nn * B * (B + 1.0);                   // Y'^T Y' (symmetric)
     if (rp.sk_d > 0) fl += nn * (double)rp.sk_zeta * B;       // sketch accumulation
-    prof_stop(tok, st, 0, by, fl);
+    prof_stop(tok, st, 0, by, fl, rp.tag);
   }
   if (launches) ++*launches;
   return note_cuda(cudaGetLastError());

@@ -58,6 +58,13 @@ def test_full_size_fp64(rbo, scheme, kappa):
     _check(rbo, torch, V0, scheme, rbo.PREC_FP64, kappa)
 
 
+@pytest.mark.parametrize("scheme", ["two", "one"])
+def test_full_size_df64(rbo, scheme):
+    import torch
+    V0 = synth.glued_blocks_torch(N, 12, 5, 1e12, seed=3, v0=True, device="cuda")
+    _check(rbo, torch, V0, scheme, rbo.PREC_DF64, 1e12)
+
+
 def test_full_size_mixed_at_kappa_1e4(rbo):
     import torch
     V0 = synth.glued_blocks_torch(N, 12, 5, 1e4, seed=2, v0=True, device="cuda")

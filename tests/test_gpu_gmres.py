@@ -91,3 +91,18 @@ def test_zero_rhs(rbo):
     Ad = rbo.DeviceCSR.from_host(A)
     x, info = rbo.sstep_gmres(Ad, torch.zeros(A.n, dtype=torch.float64, device="cuda"), s=5, m=10)
     assert info["converged"] == 1 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("s_hat", [0, 20])
+def test_poisson_df64_matches_oracle(rbo, s_hat):
+    import torch
+    A = synth.poisson3d_csr(20)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    x, info = rbo.sstep_gmres(Ad, torch.from_numpy(b).cuda(), s=5, s_hat=s_hat, m=60, tol=1e-10,
+                              precision=rbo.PREC_DF64)
+    ref = krylov.sstep_gmres(A, b, s=5, m=60, s_hat=(s_hat or None),
+                             scheme="two" if s_hat else "one", tol=1e-10)
+    assert info["converged"] == 1
+    assert abs(info["iterations"] - ref.iterations) <= (s_hat or 5)
+    assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6

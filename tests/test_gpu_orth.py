@@ -161,3 +161,33 @@ def test_mixed_precision_never_returns_silently_wrong_q(rbo, scheme, kappa):
         assert metrics.backward_error(V, Q, out.R) <= 1e-14
     else:
         assert out.info["breakdown_block"] >= 0
+
+
+@pytest.mark.parametrize("scheme,s_hat", [("one", None), ("two", 30), ("two", 60)])
+@pytest.mark.parametrize("kappa", [1e4, 1e10, 1e14])
+def test_df64_meets_the_fp64_tolerances(rbo, scheme, s_hat, kappa):
+    # float32-pair arithmetic (about 48 significant bits per operation) must give the
+    # float64-path results: orthogonality 1e-13, backward error 1e-14, and R within
+    # 1e-12 of the oracle for kappa <= 1e4
+    if s_hat == 60:
+        V = synth.glued_blocks(20000, 12, 5, kappa, seed=31)
+    else:
+        V = synth.glued_blocks(20000, 12, 5, kappa, seed=31, v0=True)
+    v0 = s_hat != 60
+    Q, out = run(rbo, scheme, V, 5, s_hat, v0=v0, precision=rbo.PREC_DF64)
+    assert out.info["status"] == 0
+    assert metrics.orth_error(Q) <= 1e-13
+    assert metrics.backward_error(V, Q, out.R) <= 1e-14
+    if kappa <= 1e4:
+        ref = oracle(scheme, V, 5, s_hat, v0=v0)
+        assert metrics.rel_diff(out.R, ref.R) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1001, 12347])
+def test_df64_ragged_sizes(rbo, n):
+    V = synth.glued_blocks(n, 12, 5, 1e8, seed=n, v0=True)
+    for scheme in ("one", "two"):
+        Q, out = run(rbo, scheme, V, 5, 30, v0=True, precision=rbo.PREC_DF64)
+        assert out.info["status"] == 0
+        assert metrics.orth_error(Q) <= 1e-13
+        assert metrics.backward_error(V, Q, out.R) <= 1e-14
