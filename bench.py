@@ -189,6 +189,14 @@ def run_ours(args):
         prof, roofline, ms_prof = None, None, None
     else:
         prof, roofline, ms_prof = profile_steps(rbo, torch, step, barrier, args)
+        if df64 is not None:
+            def step_df():
+                solve_df(0)
+                solve_df(S_HAT)
+            prof_df, _, _ = profile_steps(rbo, torch, step_df, barrier, args)
+            df64["rowpass_ms_per_step"] = prof_df["rowpass"]["ms"] / args.steps
+            df64["rowpass_by_role"] = {k: {"ms": v["ms"], "tflops": v["tflops"]}
+                                       for k, v in prof_df["rowpass_by_role"].items()}
 
     # end-to-end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(rbo, torch, A, b_host, args)

@@ -226,12 +226,16 @@ int rbo_sketch_apply(rbo_sketch sk, int64_t n, int32_t k, const double* W, int64
   cudaStream_t st = (cudaStream_t)stream;
   Arena* ar = nullptr;
   const int L = sk->d * k;
-  if ((e = arena_prepare(&ar, reduction_bytes(L) + (size_t)L * 8 + 1024))) return e;
+  const size_t tab_bytes = sketch_table_bytes(n, sk->zeta);
+  if ((e = arena_prepare(&ar, reduction_bytes(L) + (size_t)L * 8 + tab_bytes + 2048))) return e;
   if ((e = arena_reserve_reduction(ar, L, st))) return e;
   double* dout = (double*)ar->take((size_t)L * 8);
+  int16_t* tab = (int16_t*)ar->take(tab_bytes);
+  if (!dout || !tab) return RBO_ERR_NOMEM;
+  if ((e = sketch_table_launch(n, sk->d, sk->zeta, sk->seed, tab, ar->status, st))) return e;
   RowPass r;
   r.n = n; r.Y = const_cast<double*>(W); r.ldy = ldw; r.b = k;
-  r.sk_d = sk->d; r.sk_zeta = sk->zeta; r.sk_seed = sk->seed;
+  r.sk_d = sk->d; r.sk_zeta = sk->zeta; r.sk_seed = sk->seed; r.sk_tab = tab;
   r.mixed = precision == RBO_PREC_MIXED ? 1 : 0;
   r.epi.op = EPI_STORE_ALL; r.epi.out = dout; r.epi.out_sk = dout;
   int launches = 0;
@@ -313,8 +317,8 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   const int pmax = ncols;
   const int maxL = orth_max_L(pmax, kmax, d);
   Arena* ar = nullptr;
-  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d) + (size_t)ncols * ncols * 8 +
-                 4096;
+  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d, n, rand ? sk->zeta : 0) +
+                 (size_t)ncols * ncols * 8 + 4096;
   if ((e = arena_prepare(&ar, bytes))) return info_done(info, e, 0, t0);
   if ((e = arena_reserve_reduction(ar, maxL, st))) return info_done(info, e, 0, t0);
   double* Rdev = (double*)ar->take((size_t)ncols * ncols * 8);
@@ -331,7 +335,7 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
     c.zeta = sk->zeta;
     c.seed = sk->seed;
   }
-  if ((e = orth_ctx_alloc(c, pmax, kmax))) return info_done(info, e, 0, t0);
+  if ((e = orth_ctx_alloc(c, pmax, kmax, n))) return info_done(info, e, 0, t0);
   int p = 0;
   if (v0) {
     if ((e = normalise_column(c, n, V, Rdev, ncols, 0))) return info_done(info, e, c.launches, t0);

@@ -75,7 +75,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
 
   const int pmax = m + 1, kmax = K;
   const int maxL = std::max(orth_max_L(pmax, kmax, d), 1);
-  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d) +
+  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d, n, zeta) +
                  (size_t)ldq * (m + 1) * 8 + (size_t)A->nnz * 8 + 2 * (size_t)n * 8 +
                  (size_t)(m + 1) * (m + 1) * 8 + (size_t)(m + 1) * K * 8 + (size_t)m * 8 + 16 * 1024;
   Arena* ar = nullptr;
@@ -105,7 +105,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   c.d = d;
   c.zeta = zeta;
   c.seed = seed;
-  if ((e = orth_ctx_alloc(c, pmax, kmax))) return e;
+  if ((e = orth_ctx_alloc(c, pmax, kmax, n))) return e;
 
   CsrDev Araw{n, A->nnz, A->rowptr, A->col, A->val};
   CsrDev Ahat = Araw;

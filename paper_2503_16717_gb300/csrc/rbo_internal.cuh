@@ -129,6 +129,7 @@ struct RowPass {
   int acc_x = 0;                 // accumulate X^T Y'
   int acc_y = 0;                 // accumulate Y'^T Y'
   int sk_d = 0, sk_zeta = 0; uint64_t sk_seed = 0;  // accumulate S Y' (d x b)
+  const int16_t* sk_tab = nullptr;  // entries of S (sketch_table_launch), n x zeta
   int mixed = 0;                 // float32 accumulation of X^T Y' and S Y'
   int df64 = 0;                  // float32-pair arithmetic for the Gram (and small projections)
   int small_coeffs = 0;          // C is a re-orthogonalization (O(eps kappa)) coefficient block
@@ -140,6 +141,13 @@ struct RowPass {
 // Enqueue one row pass; `launches` is incremented per kernel.  Returns RBO_OK or an
 // error for invalid sizes / CUDA launch failures.
 int rowpass_launch(const RowPass& rp, Arena* ar, cudaStream_t st, int* launches);
+
+// Entry table of the sparse-sign sketch: row r of the basis (column r of S) holds
+// zeta int16 values 2 * index + (sign < 0), r = 0..n-1, row-major; the row pass
+// reads it instead of hashing.  Bytes to reserve for n rows (16-byte multiple).
+size_t sketch_table_bytes(int64_t n, int zeta);
+int sketch_table_launch(int64_t n, int d, int zeta, uint64_t seed, int16_t* tab,
+                        DevStatus* status, cudaStream_t st);
 
 // Sketch entries materialisation and a standalone sketch apply (entry points).
 int sketch_entries_launch(int64_t row0, int64_t nrows, int d, int zeta, uint64_t seed,
@@ -180,6 +188,7 @@ struct OrthCtx {
   int mixed = 0;
   int df64 = 0;   // every pass in float32-pair arithmetic where it applies
   int d = 0, zeta = 0; uint64_t seed = 0;
+  const int16_t* sk_tab = nullptr;  // sketch entry table of the call's n rows
   // small device buffers, sized once per call by orth_ctx_alloc and reused by every
   // block (stream order makes the reuse safe)
   int pmax = 0, kmax = 0;
@@ -189,9 +198,10 @@ struct OrthCtx {
 };
 // Take the small buffers from the arena for blocks with up to pmax previous columns
 // and kmax columns per block (K for two-stage).  Returns RBO_OK or RBO_ERR_NOMEM.
-int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax);
+// With a sketch (c.d > 0) it also builds the sketch entry table of n rows.
+int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax, int64_t n);
 // Arena bytes orth_ctx_alloc will need.
-size_t orth_ctx_bytes(int pmax, int kmax, int d);
+size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta);
 // Largest reduced-vector length of any pass for these sizes.
 int orth_max_L(int pmax, int kmax, int d);
 

@@ -48,7 +48,8 @@ struct PassDev {
   unsigned* tickets;
   DevStatus* status;
   // shared memory layout (byte offsets from the dynamic base)
-  int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_ent, off_red;
+  int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_red;
+  int ent_off;            // sketch entries of the tile (int16), offset inside a stage
 };
 
 // ------------------------------------------------------------------------------------
@@ -186,6 +187,11 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
       for (int t = threadIdx.x; t < d * b; t += blockDim.x) A[t] = red[P.no + t];
       __syncthreads();
       cta_householder(A, d, b, R, nullptr, beta, sg, scr);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int bad = tri_rank_deficient(R, b);
+        if (bad >= 0) set_breakdown(P.status, e.block, bad, e.stage);
+      }
       for (int t = threadIdx.x; t < b * b; t += blockDim.x) e.out_r[t] = R[t];
       break;
     }
@@ -216,6 +222,11 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
       for (int t = threadIdx.x; t < d * k; t += blockDim.x) A[t] = v[t];
       __syncthreads();
       cta_householder(A, d, k, R, Qn, beta, sg, scr);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int bad = tri_rank_deficient(R, k);
+        if (bad >= 0) set_breakdown(P.status, e.block, pp + bad, e.stage);
+      }
       for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
         int i = t % k, c = t / k;
         e.T[(pp + i) + (size_t)(pp + c) * K] = R[t];
@@ -262,7 +273,7 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
 // the kernel
 // ------------------------------------------------------------------------------------
 template <int ARITH>
-__global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ PassDev P) {
+__global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const __grid_constant__ PassDev P) {
   // ARITH 0: float64; 1: float32 for X^T Y' and the sketch (mixed precision);
   // 2: float32 pairs for the transform and the Gram, float64 for the sketch
   constexpr bool MIXED = ARITH == 1;
@@ -284,7 +295,6 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
   double* dinv = reinterpret_cast<double*>(smem + P.off_dinv);
   double* skd = reinterpret_cast<double*>(smem + P.off_sk);
   float* skf = reinterpret_cast<float*>(smem + P.off_sk);
-  int* ent = reinterpret_cast<int*>(smem + P.off_ent);
   const int d = rp.sk_d;
   const bool do_sk = d > 0;
 
@@ -355,6 +365,10 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
     return reinterpret_cast<double*>(smem + P.off_stage + (size_t)s * P.stage_bytes);
   };
   auto stage_Y = [&](int s) { return stage_X(s) + (size_t)a * TP; };
+  auto stage_E = [&](int s) {
+    return reinterpret_cast<int16_t*>(smem + P.off_stage + (size_t)s * P.stage_bytes + P.ent_off);
+  };
+  const int ent_n = do_sk ? T * rp.sk_zeta : 0;  // int16 entries per tile
 
   // bulk-copy a full tile into stage s (thread 0 only)
   auto issue_tile = [&](int tile, int s) {
@@ -362,11 +376,13 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
     double* xs = stage_X(s);
     double* ys = stage_Y(s);
     const uint32_t bytes = (uint32_t)T * 8u;
-    mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile);
+    mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile + (uint32_t)ent_n * 2u);
     for (int i = 0; i < a; ++i)
       bulk_copy_g2s(xs + (size_t)i * TP, rp.X + i * rp.ldx + r0, bytes, &bars[s]);
     for (int c = 0; c < b; ++c)
       bulk_copy_g2s(ys + (size_t)c * TP, rp.Y + c * rp.ldy + r0, bytes, &bars[s]);
+    if (ent_n > 0)
+      bulk_copy_g2s(stage_E(s), rp.sk_tab + r0 * rp.sk_zeta, (uint32_t)ent_n * 2u, &bars[s]);
   };
   auto bulk_ok = [&](int tile) {
     return P.use_bulk && ((int64_t)(tile + 1) * T <= n);
@@ -397,6 +413,9 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
         if (r < rows) v = (col < a) ? rp.X[col * rp.ldx + r0 + r] : rp.Y[(col - a) * rp.ldy + r0 + r];
         xs[(size_t)col * TP + r] = v;  // X and Y stages are contiguous
       }
+      int16_t* es = stage_E(s);
+      for (int t = tid; t < ent_n; t += NT)
+        es[t] = (t < rows * rp.sk_zeta) ? rp.sk_tab[r0 * rp.sk_zeta + t] : (int16_t)-1;
       __syncthreads();
     }
     if (timed_out) {
@@ -420,20 +439,8 @@ __global__ void __launch_bounds__(NT) rowpass_kernel(const __grid_constant__ Pas
     };
     if (df_pre) to_pairs();
 
-    // sketch entries of the tile's rows (integer hash; -1 marks rows past n)
-    if (do_sk) {
-      for (int r = tid; r < T; r += NT) {
-        int ix[ZMAX], ng[ZMAX];
-#pragma unroll
-        for (int t = 0; t < ZMAX; ++t) { ix[t] = 0; ng[t] = 0; }
-        const bool valid = r < rows;
-        if (valid && !sketch_column(rp.sk_seed, (uint64_t)(r0 + r), d, rp.sk_zeta, ix, ng))
-          set_error(P.status, RBO_ERR_SKETCH, 2);
-#pragma unroll
-        for (int t = 0; t < ZMAX; ++t)
-          if (t < rp.sk_zeta) ent[r * rp.sk_zeta + t] = valid ? (ix[t] * 2 + ng[t]) : -1;
-      }
-    }
+    // sketch entries of the tile's rows (from the entry table; -1 past n)
+    const int16_t* ent = stage_E(s);
 
     // ---- phase A: y' = transform(y), in place in the Y stage --------------------
     auto tri_solve = [&]() {
@@ -780,13 +787,14 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     arith = ok ? 2 : 0;
   }
   const int mixed = arith == 1 ? 1 : 0;
+  if (dsk > 0 && rp.sk_tab == nullptr) return RBO_ERR_ARG;
 
   // choose the tile height: largest of 64/32/16 that fits
   int T = 64;
   size_t smem = 0;
   int nsw = 0, tpo = 1, tasks = 0;
   size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_sk = 0,
-         off_ent = 0, off_red = 0;
+         ent_off = 0, off_red = 0;
   for (;;) {
     tpo = 1;
     if (items > 0)
@@ -801,7 +809,8 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
       nsw = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / std::max<size_t>(one, 1)));
     }
     off_stage = 64;
-    stage_bytes = (size_t)(rp.a + rp.b) * TP * 8;
+    ent_off = (size_t)(rp.a + rp.b) * TP * 8;  // TP even: 16-byte multiple
+    stage_bytes = ent_off + (dsk > 0 ? (((size_t)T * rp.sk_zeta * 2 + 15) & ~size_t(15)) : 0);
     size_t o = off_stage + NST * stage_bytes;
     off_c = o; o += (rp.C ? (size_t)rp.a * rp.b * 8 : 0);
     off_tri = o; o += (rp.Tri ? (size_t)rp.b * rp.b * 8 : 0);
@@ -809,7 +818,6 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     o = (o + 15) & ~size_t(15);
     off_sk = o; o += (size_t)nsw * dsk * rp.b * (mixed ? 4 : 8);
     o = (o + 15) & ~size_t(15);
-    off_ent = o; o += (dsk > 0 ? (size_t)T * ZMAX * 4 : 0);
     size_t loop_bytes = o;
     size_t comb_bytes = off_stage + (size_t)tasks * CB * 8;
     off_red = 64;
@@ -853,7 +861,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.off_tri = (int)off_tri;
   P.off_dinv = (int)off_dinv;
   P.off_sk = (int)off_sk;
-  P.off_ent = (int)off_ent;
+  P.ent_off = (int)ent_off;
   P.off_red = (int)off_red;
   P.partials = nullptr;
   P.gpart = nullptr;
@@ -910,6 +918,32 @@ __global__ void sketch_entries_kernel(int64_t row0, int64_t nrows, int d, int ze
       sign[r * zeta + t] = ng[t] ? (int8_t)-1 : (int8_t)1;
     }
   }
+}
+
+// entry table: one thread per row of the basis
+__global__ void sketch_table_kernel(int64_t n, int d, int zeta, uint64_t seed, int16_t* tab,
+                                    DevStatus* status) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int ix[ZMAX], ng[ZMAX];
+#pragma unroll
+  for (int t = 0; t < ZMAX; ++t) { ix[t] = 0; ng[t] = 0; }
+  if (!sketch_column(seed, (uint64_t)r, d, zeta, ix, ng)) set_error(status, RBO_ERR_SKETCH, 2);
+#pragma unroll
+  for (int t = 0; t < ZMAX; ++t)
+    if (t < zeta) tab[r * zeta + t] = (int16_t)(ix[t] * 2 + ng[t]);
+}
+
+size_t sketch_table_bytes(int64_t n, int zeta) {
+  return (((size_t)n * (size_t)std::max(zeta, 1) * 2) + 15) & ~size_t(15);
+}
+
+int sketch_table_launch(int64_t n, int d, int zeta, uint64_t seed, int16_t* tab, DevStatus* status,
+                        cudaStream_t st) {
+  if (n <= 0 || d < 1 || d > DMAX || zeta < 1 || zeta > ZMAX || zeta > d || !tab) return RBO_ERR_ARG;
+  const int64_t blocks = (n + 255) / 256;
+  sketch_table_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, d, zeta, seed, tab, status);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
 }
 
 int sketch_entries_launch(int64_t row0, int64_t nrows, int d, int zeta, uint64_t seed, int32_t* idx,

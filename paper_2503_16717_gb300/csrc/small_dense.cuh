@@ -45,6 +45,22 @@ __device__ int cta_cholesky(double* G, int b, int* s_flag) {
   return -1;
 }
 
+// First column j whose diagonal entry R_jj of the k x k triangular factor (ld k) is
+// not finite or within k * 2^-53 of the largest |R_ii|: the factored block is rank
+// deficient to working precision.  -1 if none.  Call from one thread.
+__device__ inline int tri_rank_deficient(const double* R, int k) {
+  double rmax = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double v = fabs(R[j + j * k]);
+    if (!(v <= 1.7976931348623157e308)) return j;  // NaN or infinity
+    rmax = fmax(rmax, v);
+  }
+  const double tol = (double)k * 0x1p-53 * rmax;
+  for (int j = 0; j < k; ++j)
+    if (!(fabs(R[j + j * k]) > tol)) return j;
+  return -1;
+}
+
 // Householder QR of A (m x k, column-major ld m) in shared memory.  On exit
 // R (k x k, ld k) holds the triangular factor with a non-negative diagonal; if Q
 // is non-null it receives the thin orthogonal factor (m x k, ld m) with the same
