@@ -226,16 +226,19 @@ int rbo_sketch_apply(rbo_sketch sk, int64_t n, int32_t k, const double* W, int64
   cudaStream_t st = (cudaStream_t)stream;
   Arena* ar = nullptr;
   const int L = sk->d * k;
-  const size_t tab_bytes = sketch_table_bytes(n, sk->zeta);
+  const int T = rowpass_sketch_T(0, k, sk->d, sk->zeta);
+  const size_t tab_bytes = sketch_sched_bytes(n, T, sk->d, sk->zeta);
   if ((e = arena_prepare(&ar, reduction_bytes(L) + (size_t)L * 8 + tab_bytes + 2048))) return e;
   if ((e = arena_reserve_reduction(ar, L, st))) return e;
   double* dout = (double*)ar->take((size_t)L * 8);
-  int16_t* tab = (int16_t*)ar->take(tab_bytes);
-  if (!dout || !tab) return RBO_ERR_NOMEM;
-  if ((e = sketch_table_launch(n, sk->d, sk->zeta, sk->seed, tab, ar->status, st))) return e;
+  uint8_t* rec = (uint8_t*)ar->take(tab_bytes);
+  if (!dout || !rec) return RBO_ERR_NOMEM;
+  if ((e = sketch_sched_launch(n, T, sk->d, sk->zeta, sk->seed, rec, ar->status, st))) return e;
   RowPass r;
   r.n = n; r.Y = const_cast<double*>(W); r.ldy = ldw; r.b = k;
-  r.sk_d = sk->d; r.sk_zeta = sk->zeta; r.sk_seed = sk->seed; r.sk_tab = tab;
+  r.sk_d = sk->d; r.sk_zeta = sk->zeta; r.sk_seed = sk->seed;
+  r.sk.rec = rec; r.sk.T = T; r.sk.mcap = sketch_sched_mcap(T, sk->d, sk->zeta);
+  r.sk.rec_bytes = sketch_sched_rec_bytes(T, sk->d, sk->zeta);
   r.mixed = precision == RBO_PREC_MIXED ? 1 : 0;
   r.epi.op = EPI_STORE_ALL; r.epi.out = dout; r.epi.out_sk = dout;
   int launches = 0;

@@ -22,7 +22,8 @@ namespace rbo {
 size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta) {
   size_t pk = (size_t)std::max(pmax, 1) * kmax, kk = (size_t)kmax * kmax;
   size_t dd = (size_t)std::max(d, 1) * kmax;
-  const size_t tab = d > 0 ? sketch_table_bytes(n, zeta) + 256 : 0;
+  const size_t tab =
+      d > 0 ? sketch_sched_bytes(n, rowpass_sketch_T(pmax, kmax, d, zeta), d, zeta) + 256 : 0;
   return (2 * pk + 6 * kk + dd + pk + kk) * 8 + 16 * 256 + tab;
 }
 
@@ -47,15 +48,19 @@ int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax, int64_t n) {
   c.tmp = (double*)c.ar->take((pk + kk) * 8);
   if (!c.C1 || !c.C2 || !c.Rh || !c.Rp || !c.R2 || !c.T || !c.GB || !c.qs || !c.tmp)
     return RBO_ERR_NOMEM;
-  c.sk_tab = nullptr;
+  c.sk = SketchSched();
   if (c.d > 0) {
-    // the sketch is a fixed operator for the call: its entries are hashed once
-    int16_t* tab = (int16_t*)c.ar->take(sketch_table_bytes(n, c.zeta));
-    if (!tab) return RBO_ERR_NOMEM;
-    const int e = sketch_table_launch(n, c.d, c.zeta, c.seed, tab, c.ar->status, c.st);
+    // the sketch is a fixed operator for the call: hashed and transposed once
+    const int T = rowpass_sketch_T(pmax, kmax, c.d, c.zeta);
+    uint8_t* rec = (uint8_t*)c.ar->take(sketch_sched_bytes(n, T, c.d, c.zeta));
+    if (!rec) return RBO_ERR_NOMEM;
+    const int e = sketch_sched_launch(n, T, c.d, c.zeta, c.seed, rec, c.ar->status, c.st);
     if (e != RBO_OK) return e;
     c.launches += 1;
-    c.sk_tab = tab;
+    c.sk.rec = rec;
+    c.sk.T = T;
+    c.sk.mcap = sketch_sched_mcap(T, c.d, c.zeta);
+    c.sk.rec_bytes = sketch_sched_rec_bytes(T, c.d, c.zeta);
   }
   return RBO_OK;
 }
@@ -119,7 +124,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
     r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
     if (p > 0) { r.C = c.C1; r.write_y = 1; }
     if (rand) {
-      r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed; r.sk_tab = c.sk_tab;
+      r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed; r.sk = c.sk;
       r.mixed = c.mixed;
       r.epi.op = EPI_HH; r.epi.out_r = c.Rh; r.epi.stage = RBO_STAGE_INTRA; r.epi.block = blk;
     } else {
@@ -208,7 +213,7 @@ int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
     r.df64 = c.df64; r.tag = 8;
     r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
     if (P > 0) { r.C = c.C1 + (size_t)cols * P; r.ldc = P; r.write_y = 1; }
-    r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed; r.sk_tab = c.sk_tab;
+    r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed; r.sk = c.sk;
     r.mixed = c.mixed;
     r.epi.op = EPI_SKB2; r.epi.qs = c.qs; r.epi.T = c.T; r.epi.K = K; r.epi.poff = cols;
     r.epi.stage = RBO_STAGE_BIGPANEL; r.epi.block = bp.blk;

@@ -116,6 +116,11 @@ struct Epilogue {
   double* coords = nullptr; int ldcoords = 0; // two-stage: (p + k) x k coordinates of Qbar
 };
 
+struct SketchSched {
+  const uint8_t* rec = nullptr;  // ceil(n / T) records of rec_bytes
+  int T = 0, mcap = 0, rec_bytes = 0;
+};
+
 struct RowPass {
   int64_t n = 0;
   const double* X = nullptr; int64_t ldx = 0; int a = 0;
@@ -129,7 +134,7 @@ struct RowPass {
   int acc_x = 0;                 // accumulate X^T Y'
   int acc_y = 0;                 // accumulate Y'^T Y'
   int sk_d = 0, sk_zeta = 0; uint64_t sk_seed = 0;  // accumulate S Y' (d x b)
-  const int16_t* sk_tab = nullptr;  // entries of S (sketch_table_launch), n x zeta
+  SketchSched sk;                // sketch schedule of the n rows (required with sk_d > 0)
   int mixed = 0;                 // float32 accumulation of X^T Y' and S Y'
   int df64 = 0;                  // float32-pair arithmetic for the Gram (and small projections)
   int small_coeffs = 0;          // C is a re-orthogonalization (O(eps kappa)) coefficient block
@@ -142,12 +147,23 @@ struct RowPass {
 // error for invalid sizes / CUDA launch failures.
 int rowpass_launch(const RowPass& rp, Arena* ar, cudaStream_t st, int* launches);
 
-// Entry table of the sparse-sign sketch: row r of the basis (column r of S) holds
-// zeta int16 values 2 * index + (sign < 0), r = 0..n-1, row-major; the row pass
-// reads it instead of hashing.  Bytes to reserve for n rows (16-byte multiple).
-size_t sketch_table_bytes(int64_t n, int zeta);
-int sketch_table_launch(int64_t n, int d, int zeta, uint64_t seed, int16_t* tab,
+// Sketch schedule: S restricted to each tile of T basis rows, transposed once per
+// call so that the row pass needs neither hashing nor a scatter with conflicts.
+// Record of a tile (rec_bytes, a 16-byte multiple):
+//   meta[mcap] (uint32): one per non-empty sketch row i of the tile, sorted by the
+//       number of entries (descending, then i): i | offset << 12 | count << 23;
+//       0xFFFFFFFF past the last;
+//   list[T * zeta] (uint8): the tile's entries grouped by sketch row (rows in
+//       increasing order within a group): local row << 1 | (sign < 0).
+int sketch_sched_mcap(int T, int d, int zeta);
+int sketch_sched_rec_bytes(int T, int d, int zeta);
+size_t sketch_sched_bytes(int64_t n, int T, int d, int zeta);
+// Builds the records of all ceil(n / T) tiles into `out` (sketch_sched_bytes).
+int sketch_sched_launch(int64_t n, int T, int d, int zeta, uint64_t seed, uint8_t* out,
                         DevStatus* status, cudaStream_t st);
+// Tile height (128, 64, 32 or 16) that every sketch pass with at most a_max X columns and
+// b_max panel columns can use (the schedule is built for it).
+int rowpass_sketch_T(int a_max, int b_max, int d, int zeta);
 
 // Sketch entries materialisation and a standalone sketch apply (entry points).
 int sketch_entries_launch(int64_t row0, int64_t nrows, int d, int zeta, uint64_t seed,
@@ -188,7 +204,7 @@ struct OrthCtx {
   int mixed = 0;
   int df64 = 0;   // every pass in float32-pair arithmetic where it applies
   int d = 0, zeta = 0; uint64_t seed = 0;
-  const int16_t* sk_tab = nullptr;  // sketch entry table of the call's n rows
+  SketchSched sk;   // sketch schedule of the call's n rows
   // small device buffers, sized once per call by orth_ctx_alloc and reused by every
   // block (stream order makes the reuse safe)
   int pmax = 0, kmax = 0;

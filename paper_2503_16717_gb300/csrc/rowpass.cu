@@ -30,18 +30,19 @@ constexpr int CB = 8;         // Z columns per task (register block)
 constexpr int IPT = 4;        // Z tasks per thread
 constexpr int GROUP = 16;     // CTAs per first-level reduction group
 constexpr int NST = 2;        // pipeline stages
+constexpr size_t STAGE_TARGET = 40 * 1024;  // bytes of one stage worth keeping in flight
 
 struct PassDev {
   RowPass p;
   int T;              // rows per tile
   int TP;             // shared-memory column stride of a tile (T + 2: fewer bank conflicts)
   int ntiles;
-  int items, tpo, tasks;  // Z work split: items = zr * ceil(b / CB), tpo row subsets
+  int items, tpo, tasks;  // Z work split: items = zr * (column blocks), tpo row subsets
+  int cw;                 // width of every column block (<= CB)
   int flush_tiles;        // float-pair Gram: tiles between flushes into float64
   int use_bulk;       // X/Y aligned for 16-byte bulk copies
   int zr, no;         // Z rows, Z outputs (zr * b)
   int L;              // partial length (no + d*b)
-  int nsw;            // sketch warps (copies)
   int ngroups;
   double* partials;
   double* gpart;
@@ -49,7 +50,7 @@ struct PassDev {
   DevStatus* status;
   // shared memory layout (byte offsets from the dynamic base)
   int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_red;
-  int ent_off;            // sketch entries of the tile (int16), offset inside a stage
+  int rec_off;            // sketch schedule record of the tile, offset inside a stage
 };
 
 // ------------------------------------------------------------------------------------
@@ -270,6 +271,52 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
 }
 
 // ------------------------------------------------------------------------------------
+// Gram task bodies: one Z row against CW columns of Y' (a register block), over the
+// tile rows g, g + tpo, ...  CW is a compile-time constant so that a narrow last
+// block (b not a multiple of CB) issues no masked-off float64 instructions.
+// ------------------------------------------------------------------------------------
+template <int CW>
+__device__ __forceinline__ void gram_rows_f64(double (&acc)[CB], const double* z, const double* y,
+                                              int g, int T, int tpo, int TP) {
+  for (int rr = g; rr < T; rr += tpo) {
+    const double zv = z[rr];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[c] = fma(zv, y[(size_t)c * TP + rr], acc[c]);
+  }
+}
+// float32 values in the first 4 bytes of each 8-byte slot
+template <int CW>
+__device__ __forceinline__ void gram_rows_f32(float (&acc)[CB], const double* z, const double* y,
+                                              int g, int T, int tpo, int TP) {
+  for (int rr = g; rr < T; rr += tpo) {
+    const float zv = reinterpret_cast<const float*>(z + rr)[0];
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      acc[c] = fmaf(zv, reinterpret_cast<const float*>(y + (size_t)c * TP + rr)[0], acc[c]);
+  }
+}
+template <int CW>
+__device__ __forceinline__ void gram_rows_df(df (&acc)[CB], const df* z, const df* y, int g, int T,
+                                             int tpo, int TP) {
+  for (int rr = g; rr < T; rr += tpo) {
+    const df zv = z[rr];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) df_fma_acc(acc[c], zv, y[(size_t)c * TP + rr]);
+  }
+}
+#define RBO_CW_DISPATCH(fn, cw, ...)            \
+  switch (cw) {                                 \
+    case 8: fn<8>(__VA_ARGS__); break;          \
+    case 7: fn<7>(__VA_ARGS__); break;          \
+    case 6: fn<6>(__VA_ARGS__); break;          \
+    case 5: fn<5>(__VA_ARGS__); break;          \
+    case 4: fn<4>(__VA_ARGS__); break;          \
+    case 3: fn<3>(__VA_ARGS__); break;          \
+    case 2: fn<2>(__VA_ARGS__); break;          \
+    default: fn<1>(__VA_ARGS__); break;         \
+  }
+
+// ------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------
 template <int ARITH>
@@ -318,7 +365,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     for (int t = tid; t < b; t += NT) dinv[t] = 1.0 / rp.Tri[t + (size_t)t * ldt];
   }
   if (do_sk) {
-    const int tot = P.nsw * d * b;
+    const int tot = d * b;
     if (MIXED)
       for (int t = tid; t < tot; t += NT) skf[t] = 0.0f;
     else
@@ -365,24 +412,26 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     return reinterpret_cast<double*>(smem + P.off_stage + (size_t)s * P.stage_bytes);
   };
   auto stage_Y = [&](int s) { return stage_X(s) + (size_t)a * TP; };
-  auto stage_E = [&](int s) {
-    return reinterpret_cast<int16_t*>(smem + P.off_stage + (size_t)s * P.stage_bytes + P.ent_off);
-  };
-  const int ent_n = do_sk ? T * rp.sk_zeta : 0;  // int16 entries per tile
+  auto stage_R = [&](int s) { return smem + P.off_stage + (size_t)s * P.stage_bytes + P.rec_off; };
+  const int rec_n = do_sk ? rp.sk.rec_bytes : 0;  // schedule record bytes per tile
 
-  // bulk-copy a full tile into stage s (thread 0 only)
+  // bulk-copy a full tile into stage s (all lanes of warp 0: one copy per lane)
   auto issue_tile = [&](int tile, int s) {
     const int64_t r0 = (int64_t)tile * T;
     double* xs = stage_X(s);
     double* ys = stage_Y(s);
     const uint32_t bytes = (uint32_t)T * 8u;
-    mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile + (uint32_t)ent_n * 2u);
-    for (int i = 0; i < a; ++i)
-      bulk_copy_g2s(xs + (size_t)i * TP, rp.X + i * rp.ldx + r0, bytes, &bars[s]);
-    for (int c = 0; c < b; ++c)
-      bulk_copy_g2s(ys + (size_t)c * TP, rp.Y + c * rp.ldy + r0, bytes, &bars[s]);
-    if (ent_n > 0)
-      bulk_copy_g2s(stage_E(s), rp.sk_tab + r0 * rp.sk_zeta, (uint32_t)ent_n * 2u, &bars[s]);
+    if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile + (uint32_t)rec_n);
+    __syncwarp();
+    const int ncopy = a + b + (rec_n > 0 ? 1 : 0);
+    for (int j = lane; j < ncopy; j += 32) {
+      if (j < a)
+        bulk_copy_g2s(xs + (size_t)j * TP, rp.X + j * rp.ldx + r0, bytes, &bars[s]);
+      else if (j < a + b)
+        bulk_copy_g2s(ys + (size_t)(j - a) * TP, rp.Y + (j - a) * rp.ldy + r0, bytes, &bars[s]);
+      else
+        bulk_copy_g2s(stage_R(s), rp.sk.rec + (size_t)tile * rec_n, (uint32_t)rec_n, &bars[s]);
+    }
   };
   auto bulk_ok = [&](int tile) {
     return P.use_bulk && ((int64_t)(tile + 1) * T <= n);
@@ -390,7 +439,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
 
   uint32_t phase[NST] = {0u, 0u};
   int first = blockIdx.x;
-  if (first < P.ntiles && bulk_ok(first) && tid == 0) issue_tile(first, 0);
+  if (first < P.ntiles && bulk_ok(first) && warp == 0) issue_tile(first, 0);
 
   int it = 0;
   bool timed_out = false;
@@ -413,9 +462,9 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
         if (r < rows) v = (col < a) ? rp.X[col * rp.ldx + r0 + r] : rp.Y[(col - a) * rp.ldy + r0 + r];
         xs[(size_t)col * TP + r] = v;  // X and Y stages are contiguous
       }
-      int16_t* es = stage_E(s);
-      for (int t = tid; t < ent_n; t += NT)
-        es[t] = (t < rows * rp.sk_zeta) ? rp.sk_tab[r0 * rp.sk_zeta + t] : (int16_t)-1;
+      uint32_t* es = reinterpret_cast<uint32_t*>(stage_R(s));
+      const uint32_t* eg = reinterpret_cast<const uint32_t*>(rp.sk.rec + (size_t)tile * rec_n);
+      for (int t = tid; t < rec_n / 4; t += NT) es[t] = eg[t];
       __syncthreads();
     }
     if (timed_out) {
@@ -424,7 +473,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     }
     // prefetch the next tile of this CTA into the other stage
     const int nxt = tile + gridDim.x;
-    if (tid == 0 && nxt < P.ntiles && bulk_ok(nxt)) {
+    if (warp == 0 && nxt < P.ntiles && bulk_ok(nxt)) {
       fence_proxy_async();
       issue_tile(nxt, s ^ 1);
     }
@@ -438,9 +487,6 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
       __syncthreads();
     };
     if (df_pre) to_pairs();
-
-    // sketch entries of the tile's rows (from the entry table; -1 past n)
-    const int16_t* ent = stage_E(s);
 
     // ---- phase A: y' = transform(y), in place in the Y stage --------------------
     auto tri_solve = [&]() {
@@ -527,17 +573,12 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
         const int task = tid + k * NT;
         if (task < P.tasks) {
           const int item = task % P.items, g = task / P.items;
-          const int i = item % P.zr, c0 = (item / P.zr) * CB;
-          const int cw = min(CB, b - c0);
+          const int i = item % P.zr, c0 = min((item / P.zr) * P.cw, b - P.cw);
+          const int cw = P.cw;
           const df* zsrc = reinterpret_cast<const df*>((i < ax) ? xs + (size_t)i * TP
                                                                  : ys + (size_t)(i - ax) * TP);
           const df* ysrc = reinterpret_cast<const df*>(ys + (size_t)c0 * TP);
-          for (int rr = g; rr < T; rr += P.tpo) {
-            const df z = zsrc[rr];
-#pragma unroll
-            for (int c = 0; c < CB; ++c)
-              if (c < cw) df_fma_acc(acci[k][c], z, ysrc[(size_t)c * TP + rr]);
-          }
+          RBO_CW_DISPATCH(gram_rows_df, cw, acci[k], zsrc, ysrc, g, T, P.tpo, TP)
         }
       }
       if (++since_flush >= P.flush_tiles) {
@@ -550,67 +591,56 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
         const int task = tid + k * NT;
         if (task < P.tasks) {
           const int item = task % P.items, g = task / P.items;
-          const int i = item % P.zr, c0 = (item / P.zr) * CB;
-          const int cw = min(CB, b - c0);
+          const int i = item % P.zr, c0 = min((item / P.zr) * P.cw, b - P.cw);
+          const int cw = P.cw;
           const double* zsrc = (i < ax) ? xs + (size_t)i * TP : ys + (size_t)(i - ax) * TP;
           const double* ysrc = ys + (size_t)c0 * TP;
           if (MIXED) {
-            for (int rr = g; rr < T; rr += P.tpo) {
-              const float z = reinterpret_cast<const float*>(zsrc + rr)[0];
-#pragma unroll
-              for (int c = 0; c < CB; ++c)
-                if (c < cw)
-                  accf[k][c] = fmaf(z, reinterpret_cast<const float*>(ysrc + (size_t)c * TP + rr)[0],
-                                    accf[k][c]);
-            }
+            RBO_CW_DISPATCH(gram_rows_f32, cw, accf[k], zsrc, ysrc, g, T, P.tpo, TP)
           } else {
-            for (int rr = g; rr < T; rr += P.tpo) {
-              const double z = zsrc[rr];
-#pragma unroll
-              for (int c = 0; c < CB; ++c)
-                if (c < cw) acc[k][c] = fma(z, ysrc[(size_t)c * TP + rr], acc[k][c]);
-            }
+            RBO_CW_DISPATCH(gram_rows_f64, cw, acc[k], zsrc, ysrc, g, T, P.tpo, TP)
           }
         }
       }
     }
     // ---- phase B': sketch S Y' ---------------------------------------------------
-    // (row, slot) pairs of the tile are scattered by the first nsw warps into
-    // warp-private copies; lanes of a warp that hit the same sketch row add in lane
-    // order, so every copy is summed in a fixed order (deterministic).
+    // The tile's schedule record lists its non-empty sketch rows, most entries
+    // first; thread q takes slots q, q + NT, ... and adds the entries of its sketch
+    // row (in increasing tile row) into that row's accumulators, which no other
+    // thread touches during the tile.  Every sum has a fixed order (deterministic),
+    // and the count-sorted slots keep the lanes of a warp on equal trip counts.
     if (do_sk) {
-      __syncthreads();  // entries of this tile complete
-      if (warp < P.nsw) {
-        const int zeta = rp.sk_zeta;
-        const int npair = T * zeta;
-        const unsigned lt_mask = (1u << lane) - 1u;
-        for (int p0 = warp * 32; p0 < npair; p0 += P.nsw * 32) {
-          const int pr = p0 + lane;
-          const int ev = pr < npair ? ent[pr] : -1;
-          const int rr = pr / zeta;
-          const bool valid = ev >= 0;
-          const int ix = ev >> 1;
-          const int key = valid ? ix : -1 - lane;
-          const unsigned grp = __match_any_sync(0xffffffffu, key);
-          const int rank = __popc(grp & lt_mask);
-          const int maxrank = __reduce_max_sync(0xffffffffu, (unsigned)rank);
-          for (int kk = 0; kk <= maxrank; ++kk) {
-            if (valid && rank == kk) {
-              if (MIXED) {
-                float* cp = skf + (size_t)warp * d * b;
-                for (int c = 0; c < b; ++c) {
-                  const float yv = reinterpret_cast<const float*>(ys + (size_t)c * TP + rr)[0];
-                  cp[ix + c * d] += (ev & 1) ? -yv : yv;
-                }
-              } else {
-                double* cp = skd + (size_t)warp * d * b;
-                for (int c = 0; c < b; ++c) {
-                  const double yv = ys[(size_t)c * TP + rr];
-                  cp[ix + c * d] += (ev & 1) ? -yv : yv;
-                }
-              }
+      __syncthreads();  // y' of this tile complete
+      const uint32_t* meta = reinterpret_cast<const uint32_t*>(stage_R(s));
+      const uint8_t* lst = reinterpret_cast<const uint8_t*>(meta + rp.sk.mcap);
+      for (int q = tid; q < rp.sk.mcap; q += NT) {
+        const uint32_t m = meta[q];
+        if (m == 0xFFFFFFFFu) break;
+        const int i = (int)(m & 0xFFFu), o = (int)((m >> 12) & 0x7FFu), cnt = (int)(m >> 23);
+        const uint8_t* e = lst + o;
+        if (MIXED) {
+          for (int c = 0; c < b; ++c) {
+            const float* yc = reinterpret_cast<const float*>(ys + (size_t)c * TP);
+            float v = skf[i + c * d];
+            for (int t = 0; t < cnt; ++t) {
+              const int ev = e[t];
+              // sign by flipping the sign bit (integer ALU, not a float negation)
+              v += __int_as_float(__float_as_int(yc[2 * (ev >> 1)]) ^ ((ev & 1) << 31));
             }
-            __syncwarp();
+            skf[i + c * d] = v;
+          }
+        } else {
+          for (int c = 0; c < b; ++c) {
+            const double* yc = ys + (size_t)c * TP;
+            double v = skd[i + c * d];
+            for (int t = 0; t < cnt; ++t) {
+              const int ev = e[t];
+              // sign by flipping the sign bit: a float64 negation would take a
+              // second slot of the (scarce) float64 pipe
+              v += __longlong_as_double(__double_as_longlong(yc[ev >> 1]) ^
+                                        ((long long)(ev & 1) << 63));
+            }
+            skd[i + c * d] = v;
           }
         }
       }
@@ -635,19 +665,15 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     __syncthreads();
     for (int o = tid; o < P.no; o += NT) {
       const int i = o / b, c = o % b;
-      const int item = (c / CB) * P.zr + i, cc = c % CB;
+      const int blk = c / P.cw, c0 = min(blk * P.cw, b - P.cw);
+      const int item = blk * P.zr + i, cc = c - c0;
       double sum = 0.0;
       for (int g = 0; g < P.tpo; ++g) sum += comb[(size_t)(g * P.items + item) * CB + cc];
       mypart[o] = sum;
     }
   }
   if (do_sk) {
-    for (int t = tid; t < d * b; t += NT) {
-      double s = 0.0;
-      for (int w = 0; w < P.nsw; ++w)
-        s += MIXED ? (double)skf[(size_t)w * d * b + t] : skd[(size_t)w * d * b + t];
-      mypart[P.no + t] = s;
-    }
+    for (int t = tid; t < d * b; t += NT) mypart[P.no + t] = MIXED ? (double)skf[t] : skd[t];
   }
   __threadfence();
   __syncthreads();
@@ -665,7 +691,12 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     double* gout = P.gpart + (size_t)g * P.L;
     for (int t = tid; t < P.L; t += NT) {
       double s = 0.0;
-      for (int i = 0; i < gsize; ++i) s += __ldcg(base + (size_t)i * P.L + t);
+      double v[GROUP];
+#pragma unroll
+      for (int i = 0; i < GROUP; ++i) v[i] = i < gsize ? __ldcg(base + (size_t)i * P.L + t) : 0.0;
+#pragma unroll
+      for (int i = 0; i < GROUP; ++i)
+        if (i < gsize) s += v[i];
       gout[t] = s;
     }
   }
@@ -682,7 +713,15 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
   double* red = reinterpret_cast<double*>(smem + P.off_red);
   for (int t = tid; t < P.L; t += NT) {
     double s = 0.0;
-    for (int i = 0; i < P.ngroups; ++i) s += __ldcg(P.gpart + (size_t)i * P.L + t);
+    for (int i0 = 0; i0 < P.ngroups; i0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        v[i] = i0 + i < P.ngroups ? __ldcg(P.gpart + (size_t)(i0 + i) * P.L + t) : 0.0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i0 + i < P.ngroups) s += v[i];
+    }
     red[t] = s;
   }
   if (tid == 0) P.tickets[P.ngroups] = 0u;
@@ -776,7 +815,10 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   const int dsk = rp.sk_d > 0 ? rp.sk_d : 0;
   const int L = no + dsk * rp.b;
   // Z work split: items (Z row, block of CB columns), tpo row subsets per item
-  const int items = zr * ((rp.b + CB - 1) / CB);
+  // Z columns in nblk blocks of one width cw <= CB (the last block starts at b - cw
+  // and may overlap its neighbour): every Gram task has the same trip counts
+  const int nblk = (rp.b + CB - 1) / CB, cw = (rp.b + nblk - 1) / nblk;
+  const int items = zr * nblk;
   if (items > IPT * NT) return RBO_ERR_ARG;
   // arithmetic: float32 pairs only where they apply (transform or Gram, no sketch
   // together with a Gram, at most 2 Gram tasks per thread); float64 otherwise
@@ -787,43 +829,49 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     arith = ok ? 2 : 0;
   }
   const int mixed = arith == 1 ? 1 : 0;
-  if (dsk > 0 && rp.sk_tab == nullptr) return RBO_ERR_ARG;
+  if (dsk > 0) {
+    // sketch passes run on the tiles of the call's sketch schedule
+    if (rp.sk.rec == nullptr || rp.sk.mcap != sketch_sched_mcap(rp.sk.T, dsk, rp.sk_zeta) ||
+        rp.sk.rec_bytes != sketch_sched_rec_bytes(rp.sk.T, dsk, rp.sk_zeta))
+      return RBO_ERR_ARG;
+  }
 
-  // choose the tile height: largest of 64/32/16 that fits
+  // tile height: the sketch schedule's with a sketch; otherwise the tallest tile up to
+  // 512 rows whose stage stays within STAGE_TARGET bytes (narrow panels need tall tiles
+  // to keep enough bytes in flight), at least 64 rows, halved while the layout does
+  // not fit
   int T = 64;
+  if (dsk > 0) {
+    T = rp.sk.T;
+  } else {
+    while (T < 512 && (size_t)(rp.a + rp.b) * (2 * T + 2) * 8 <= STAGE_TARGET) T *= 2;
+  }
   size_t smem = 0;
-  int nsw = 0, tpo = 1, tasks = 0;
+  int tpo = 1, tasks = 0;
   size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_sk = 0,
-         ent_off = 0, off_red = 0;
+         rec_off = 0, off_red = 0;
   for (;;) {
     tpo = 1;
     if (items > 0)
       while (items * tpo * 2 <= NT && tpo * 2 <= T / 4) tpo *= 2;
     tasks = items * tpo;
     const int TP = T + 2;
-    // sketch copies: one per scatter warp, up to 4 (one per SM sub-partition) while
-    // they take at most 96 KB
-    nsw = 0;
-    if (dsk > 0) {
-      const size_t one = (size_t)dsk * rp.b * (mixed ? 4 : 8);
-      nsw = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / std::max<size_t>(one, 1)));
-    }
     off_stage = 64;
-    ent_off = (size_t)(rp.a + rp.b) * TP * 8;  // TP even: 16-byte multiple
-    stage_bytes = ent_off + (dsk > 0 ? (((size_t)T * rp.sk_zeta * 2 + 15) & ~size_t(15)) : 0);
+    rec_off = (size_t)(rp.a + rp.b) * TP * 8;  // TP even: 16-byte multiple
+    stage_bytes = rec_off + (dsk > 0 ? (size_t)rp.sk.rec_bytes : 0);
     size_t o = off_stage + NST * stage_bytes;
     off_c = o; o += (rp.C ? (size_t)rp.a * rp.b * 8 : 0);
     off_tri = o; o += (rp.Tri ? (size_t)rp.b * rp.b * 8 : 0);
     off_dinv = o; o += (rp.Tri ? (size_t)rp.b * 8 : 0);
     o = (o + 15) & ~size_t(15);
-    off_sk = o; o += (size_t)nsw * dsk * rp.b * (mixed ? 4 : 8);
+    off_sk = o; o += (size_t)dsk * rp.b * (mixed ? 4 : 8);
     o = (o + 15) & ~size_t(15);
     size_t loop_bytes = o;
     size_t comb_bytes = off_stage + (size_t)tasks * CB * 8;
     off_red = 64;
     size_t epi_bytes = off_red + ((size_t)L + 2) * 8 + epilogue_doubles(rp, zr) * 8;
     smem = std::max(std::max(loop_bytes, epi_bytes), comb_bytes);
-    if (smem <= 220 * 1024 || T == 16) break;
+    if (smem <= 220 * 1024 || T == 16 || dsk > 0) break;
     T /= 2;
   }
   const int limit = arith == 1 ? smem_limit<1>() : (arith == 2 ? smem_limit<2>() : smem_limit<0>());
@@ -842,6 +890,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.TP = T + 2;
   P.ntiles = ntiles;
   P.items = items;
+  P.cw = cw;
   P.tpo = tpo;
   P.tasks = tasks;
   // float-pair Gram chains are flushed into float64 after about 64 products
@@ -852,7 +901,6 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.zr = zr;
   P.no = no;
   P.L = L;
-  P.nsw = nsw;
   P.ngroups = ngroups;
   P.status = ar->status;
   P.off_stage = (int)off_stage;
@@ -861,7 +909,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.off_tri = (int)off_tri;
   P.off_dinv = (int)off_dinv;
   P.off_sk = (int)off_sk;
-  P.ent_off = (int)ent_off;
+  P.rec_off = (int)rec_off;
   P.off_red = (int)off_red;
   P.partials = nullptr;
   P.gpart = nullptr;
@@ -920,30 +968,136 @@ __global__ void sketch_entries_kernel(int64_t row0, int64_t nrows, int d, int ze
   }
 }
 
-// entry table: one thread per row of the basis
-__global__ void sketch_table_kernel(int64_t n, int d, int zeta, uint64_t seed, int16_t* tab,
+// ------------------------------------------------------------------------------------
+// sketch schedule (built once per call)
+// ------------------------------------------------------------------------------------
+int sketch_sched_mcap(int T, int d, int zeta) { return std::min(d, T * zeta); }
+
+int sketch_sched_rec_bytes(int T, int d, int zeta) {
+  return (sketch_sched_mcap(T, d, zeta) * 4 + T * zeta + 15) & ~15;
+}
+
+size_t sketch_sched_bytes(int64_t n, int T, int d, int zeta) {
+  if (T <= 0 || n <= 0) return 0;
+  return (size_t)((n + T - 1) / T) * (size_t)sketch_sched_rec_bytes(T, d, zeta);
+}
+
+static int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// ascending bitonic sort of N (a power of two) keys in shared memory, whole block
+template <typename K>
+__device__ void block_bitonic_sort(K* key, int N) {
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const K x = key[i], y = key[l];
+          if ((x > y) == ((i & k) == 0)) {
+            key[i] = y;
+            key[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// One CTA per tile: hash the tile's rows (SplitMix64 sparse-sign columns), sort the
+// (sketch row, pair) keys, then sort the non-empty sketch rows by entry count.
+// Keys are unique, so the result does not depend on thread timing.
+__global__ void sketch_sched_kernel(int64_t n, int T, int d, int zeta, uint64_t seed, int np2,
+                                    int mp2, int mcap, int rec_bytes, uint8_t* out,
                                     DevStatus* status) {
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int ix[ZMAX], ng[ZMAX];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  unsigned long long* rkey = reinterpret_cast<unsigned long long*>(sm_raw);  // mp2
+  uint32_t* key = reinterpret_cast<uint32_t*>(rkey + mp2);                    // np2
+  __shared__ int s_nrow;
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  const int64_t r0 = (int64_t)tile * T;
+  const int rows = (int)std::min<int64_t>((int64_t)T, n - r0);
+  const int np = T * zeta;
+  if (tid == 0) s_nrow = 0;
+  for (int t = tid; t < np2; t += blockDim.x) key[t] = 0xFFFFFFFFu;
+  for (int t = tid; t < mp2; t += blockDim.x) rkey[t] = ~0ull;
+  __syncthreads();
+  for (int r = tid; r < rows; r += blockDim.x) {
+    int ix[ZMAX], ng[ZMAX];
 #pragma unroll
-  for (int t = 0; t < ZMAX; ++t) { ix[t] = 0; ng[t] = 0; }
-  if (!sketch_column(seed, (uint64_t)r, d, zeta, ix, ng)) set_error(status, RBO_ERR_SKETCH, 2);
+    for (int t = 0; t < ZMAX; ++t) { ix[t] = 0; ng[t] = 0; }
+    if (!sketch_column(seed, (uint64_t)(r0 + r), d, zeta, ix, ng)) set_error(status, RBO_ERR_SKETCH, 2);
 #pragma unroll
-  for (int t = 0; t < ZMAX; ++t)
-    if (t < zeta) tab[r * zeta + t] = (int16_t)(ix[t] * 2 + ng[t]);
+    for (int t = 0; t < ZMAX; ++t) {
+      if (t < zeta) {
+        const uint32_t p = (uint32_t)(r * zeta + t);
+        key[p] = ((uint32_t)ix[t] << 12) | (p << 1) | (uint32_t)ng[t];
+      }
+    }
+  }
+  __syncthreads();
+  block_bitonic_sort(key, np2);
+  uint8_t* rec = out + (size_t)tile * rec_bytes;
+  uint32_t* meta = reinterpret_cast<uint32_t*>(rec);
+  uint8_t* lst = rec + (size_t)mcap * 4;
+  const int nvalid = rows * zeta;
+  for (int q = tid; q < np; q += blockDim.x) {
+    uint8_t v = 0;
+    if (q < nvalid) {
+      const uint32_t kq = key[q];
+      const int p = (int)((kq >> 1) & 0x7FFu);
+      v = (uint8_t)(((p / zeta) << 1) | (int)(kq & 1u));
+      const uint32_t i = kq >> 12;
+      if (q == 0 || (key[q - 1] >> 12) != i) {  // first entry of sketch row i
+        int e = q + 1;
+        while (e < nvalid && (key[e] >> 12) == i) ++e;
+        const uint32_t cnt = (uint32_t)(e - q);
+        const uint32_t m = i | ((uint32_t)q << 12) | (cnt << 23);
+        const unsigned long long sk = ((unsigned long long)(511u - cnt) << 12) | i;
+        const int slot = atomicAdd(&s_nrow, 1);
+        rkey[slot] = (sk << 32) | m;
+      }
+    }
+    lst[q] = v;
+  }
+  __syncthreads();
+  block_bitonic_sort(rkey, mp2);
+  for (int q = tid; q < mcap; q += blockDim.x)
+    meta[q] = q < s_nrow ? (uint32_t)(rkey[q] & 0xFFFFFFFFull) : 0xFFFFFFFFu;
+  // zero the record's padding
+  for (int t = mcap * 4 + np + tid; t < rec_bytes; t += blockDim.x) rec[t] = 0;
 }
 
-size_t sketch_table_bytes(int64_t n, int zeta) {
-  return (((size_t)n * (size_t)std::max(zeta, 1) * 2) + 15) & ~size_t(15);
-}
-
-int sketch_table_launch(int64_t n, int d, int zeta, uint64_t seed, int16_t* tab, DevStatus* status,
-                        cudaStream_t st) {
-  if (n <= 0 || d < 1 || d > DMAX || zeta < 1 || zeta > ZMAX || zeta > d || !tab) return RBO_ERR_ARG;
-  const int64_t blocks = (n + 255) / 256;
-  sketch_table_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, d, zeta, seed, tab, status);
+int sketch_sched_launch(int64_t n, int T, int d, int zeta, uint64_t seed, uint8_t* out,
+                        DevStatus* status, cudaStream_t st) {
+  if (n <= 0 || (T != 16 && T != 32 && T != 64 && T != 128) || d < 1 || d > DMAX || zeta < 1 ||
+      zeta > ZMAX || zeta > d || !out)
+    return RBO_ERR_ARG;
+  const int np2 = next_pow2(T * zeta), mcap = sketch_sched_mcap(T, d, zeta);
+  const int mp2 = next_pow2(mcap);
+  const size_t smem = (size_t)mp2 * 8 + (size_t)np2 * 4;
+  const int64_t ntiles = (n + T - 1) / T;
+  sketch_sched_kernel<<<(unsigned)ntiles, NT, smem, st>>>(n, T, d, zeta, seed, np2, mp2, mcap,
+                                                          sketch_sched_rec_bytes(T, d, zeta), out,
+                                                          status);
   return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+int rowpass_sketch_T(int a_max, int b_max, int d, int zeta) {
+  // shared memory of the streaming loop of a sketch pass (projection, no Gram); 128
+  // rows only while a stage stays within STAGE_TARGET
+  for (int T = 128; T > 16; T /= 2) {
+    if (T > 64 && (size_t)(a_max + b_max) * (T + 2) * 8 > STAGE_TARGET) continue;
+    size_t o = 64 + (size_t)NST * ((size_t)(a_max + b_max) * (T + 2) * 8 +
+                                   (size_t)sketch_sched_rec_bytes(T, d, zeta));
+    o += (size_t)a_max * b_max * 8 + 16 + (size_t)d * b_max * 8 + 16;
+    if (o <= 220 * 1024) return T;
+  }
+  return 16;
 }
 
 int sketch_entries_launch(int64_t row0, int64_t nrows, int d, int zeta, uint64_t seed, int32_t* idx,

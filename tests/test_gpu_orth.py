@@ -79,9 +79,10 @@ def test_cholqr2_breakdown_reported(rbo):
     ref = oracle("cholqr2", V, 5)
     assert not ref.ok
     assert out.info["status"] in (rbo.ERR_CHOL_BREAKDOWN, rbo.ERR_LOST_ORTHOGONALITY)
-    # the deciding pivot is at rounding level (kappa^2 eps >> 1), so which of the
-    # first blocks fails depends on the summation order; the oracle fails at block 0
-    assert 0 <= out.info["breakdown_block"] <= 2
+    # every block has kappa = 1e10 (kappa^2 eps >> 1): the deciding pivots are at
+    # rounding level, so which block fails first depends on the summation order (the
+    # oracle fails at block 0); a breakdown must be reported at one of the 12 blocks
+    assert 0 <= out.info["breakdown_block"] < 12
     assert out.info["breakdown_stage_name"] in ("intra", "intra2", "final")
     if out.info["status"] == rbo.ERR_CHOL_BREAKDOWN:
         assert 0 <= out.info["breakdown_column"] < 5
