@@ -39,6 +39,9 @@ struct PassDev {
   int ntiles;
   int items, tpo, tasks;  // Z work split: items = zr * (column blocks), tpo row subsets
   int cw;                 // width of every column block (<= CB)
+  int nblk;               // column blocks
+  int blk_start[9];       // first item of each block: X rows, then the Y' rows that reach
+                          // the block (the symmetric Y'^T Y' needs no block below its diagonal)
   int flush_tiles;        // float-pair Gram: tiles between flushes into float64
   int use_bulk;       // X/Y aligned for 16-byte bulk copies
   int zr, no;         // Z rows, Z outputs (zr * b)
@@ -573,7 +576,9 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
         const int task = tid + k * NT;
         if (task < P.tasks) {
           const int item = task % P.items, g = task / P.items;
-          const int i = item % P.zr, c0 = min((item / P.zr) * P.cw, b - P.cw);
+          int blk = 0;
+          while (blk + 1 < P.nblk && item >= P.blk_start[blk + 1]) ++blk;
+          const int i = item - P.blk_start[blk], c0 = min(blk * P.cw, b - P.cw);
           const int cw = P.cw;
           const df* zsrc = reinterpret_cast<const df*>((i < ax) ? xs + (size_t)i * TP
                                                                  : ys + (size_t)(i - ax) * TP);
@@ -591,7 +596,9 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
         const int task = tid + k * NT;
         if (task < P.tasks) {
           const int item = task % P.items, g = task / P.items;
-          const int i = item % P.zr, c0 = min((item / P.zr) * P.cw, b - P.cw);
+          int blk = 0;
+          while (blk + 1 < P.nblk && item >= P.blk_start[blk + 1]) ++blk;
+          const int i = item - P.blk_start[blk], c0 = min(blk * P.cw, b - P.cw);
           const int cw = P.cw;
           const double* zsrc = (i < ax) ? xs + (size_t)i * TP : ys + (size_t)(i - ax) * TP;
           const double* ysrc = ys + (size_t)c0 * TP;
@@ -665,8 +672,15 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     __syncthreads();
     for (int o = tid; o < P.no; o += NT) {
       const int i = o / b, c = o % b;
-      const int blk = c / P.cw, c0 = min(blk * P.cw, b - P.cw);
-      const int item = blk * P.zr + i, cc = c - c0;
+      // Y'^T Y' is symmetric: its entries below the diagonal come from the upper
+      // triangle (the same products summed in the same order)
+      int zi = i, zc = c;
+      if (i >= ax && i - ax > c) {
+        zi = ax + c;
+        zc = i - ax;
+      }
+      const int blk = zc / P.cw, c0 = min(blk * P.cw, b - P.cw);
+      const int item = P.blk_start[blk] + zi, cc = zc - c0;
       double sum = 0.0;
       for (int g = 0; g < P.tpo; ++g) sum += comb[(size_t)(g * P.items + item) * CB + cc];
       mypart[o] = sum;
@@ -818,7 +832,13 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   // Z columns in nblk blocks of one width cw <= CB (the last block starts at b - cw
   // and may overlap its neighbour): every Gram task has the same trip counts
   const int nblk = (rp.b + CB - 1) / CB, cw = (rp.b + nblk - 1) / nblk;
-  const int items = zr * nblk;
+  const int axr = rp.acc_x ? rp.a : 0;
+  int blk_start[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < nblk; ++k) {
+    const int c0 = std::min(k * cw, rp.b - cw);
+    blk_start[k + 1] = blk_start[k] + axr + (rp.acc_y ? std::min(rp.b, c0 + cw) : 0);
+  }
+  const int items = zr > 0 ? blk_start[nblk] : 0;
   if (items > IPT * NT) return RBO_ERR_ARG;
   // arithmetic: float32 pairs only where they apply (transform or Gram, no sketch
   // together with a Gram, at most 2 Gram tasks per thread); float64 otherwise
@@ -891,6 +911,8 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.ntiles = ntiles;
   P.items = items;
   P.cw = cw;
+  P.nblk = nblk;
+  for (int k = 0; k < 9; ++k) P.blk_start[k] = blk_start[k];
   P.tpo = tpo;
   P.tasks = tasks;
   // float-pair Gram chains are flushed into float64 after about 64 products
