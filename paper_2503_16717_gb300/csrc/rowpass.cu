@@ -492,13 +492,30 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     if (df_pre) to_pairs();
 
     // ---- phase A: y' = transform(y), in place in the Y stage --------------------
+    // y' = y Tri^-1 by rows, in column blocks of CB: the block's update by the
+    // finished columns runs over all (row, column) pairs, the substitution inside the
+    // block over rows.  Each entry subtracts its terms in column order, as an
+    // unblocked row-by-row substitution would.
     auto tri_solve = [&]() {
-      for (int r = tid; r < T; r += NT) {
-        for (int c = 0; c < b; ++c) {
-          double v = ys[c * TP + r];
-          for (int i = 0; i < c; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
-          ys[c * TP + r] = v * dinv[c];
+      for (int c0 = 0; c0 < b; c0 += CB) {
+        const int cw = min(CB, b - c0);
+        if (c0 > 0) {
+          for (int t = tid; t < T * cw; t += NT) {
+            const int r = t % T, c = c0 + t / T;
+            double v = ys[c * TP + r];
+            for (int i = 0; i < c0; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
+            ys[c * TP + r] = v;
+          }
+          __syncthreads();
         }
+        for (int r = tid; r < T; r += NT) {
+          for (int c = c0; c < c0 + cw; ++c) {
+            double v = ys[c * TP + r];
+            for (int i = c0; i < c; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
+            ys[c * TP + r] = v * dinv[c];
+          }
+        }
+        if (c0 + CB < b) __syncthreads();
       }
     };
     auto project = [&]() {

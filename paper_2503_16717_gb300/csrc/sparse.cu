@@ -32,14 +32,48 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, int64_t nnz,
       if (status && sub == 0) set_error(status, RBO_ERR_ARG, 11);
       end = beg;
     }
-    for (int j = beg + sub; j < end; j += LPR) {
-      const int cj = __ldg(col + j);
-      if (cj < 0 || (int64_t)cj >= n) {
-        if (status) set_error(status, RBO_ERR_ARG, 12);
-        continue;
+    if (LPR == 1) {
+      // one thread per row (short rows): the row's indices and values are loaded in
+      // groups of 8 ahead of the gathers, and no cross-lane reduction is needed (each
+      // float64 operation costs a slot of this GPU's narrow float64 pipe)
+      for (int j0 = beg; j0 < end; j0 += 8) {
+        int cj[8];
+        double vj[8], xj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cj[u] = -1;
+          vj[u] = 0.0;
+          if (j0 + u < end) {
+            cj[u] = __ldg(col + j0 + u);
+            vj[u] = __ldg(val + j0 + u);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          xj[u] = 0.0;
+          if (j0 + u < end) {
+            if (cj[u] < 0 || (int64_t)cj[u] >= n) {
+              if (status) set_error(status, RBO_ERR_ARG, 12);
+              cj[u] = -1;
+            } else {
+              xj[u] = dscale ? __ldg(dscale + cj[u]) * __ldg(x + cj[u]) : __ldg(x + cj[u]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + u < end && cj[u] >= 0) s = fma(vj[u], xj[u], s);
       }
-      const double xv = dscale ? __ldg(dscale + cj) * __ldg(x + cj) : __ldg(x + cj);
-      s = fma(__ldg(val + j), xv, s);
+    } else {
+      for (int j = beg + sub; j < end; j += LPR) {
+        const int cj = __ldg(col + j);
+        if (cj < 0 || (int64_t)cj >= n) {
+          if (status) set_error(status, RBO_ERR_ARG, 12);
+          continue;
+        }
+        const double xv = dscale ? __ldg(dscale + cj) * __ldg(x + cj) : __ldg(x + cj);
+        s = fma(__ldg(val + j), xv, s);
+      }
     }
   }
 #pragma unroll
@@ -75,8 +109,8 @@ static int spmv_dispatch(const CsrDev& A, const double* dscale, const double* x,
 static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
                                const double* b, double* y, DevStatus* status, cudaStream_t st) {
   const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
-  if (avg <= 8.0)
-    spmv_go<4>(A, dscale, x, b, y, status, st);
+  if (avg <= 12.0)
+    spmv_go<1>(A, dscale, x, b, y, status, st);
   else if (avg <= 24.0)
     spmv_go<8>(A, dscale, x, b, y, status, st);
   else
