@@ -307,6 +307,43 @@ __device__ __forceinline__ void gram_rows_df(df (&acc)[CB], const df* z, const d
     for (int c = 0; c < CW; ++c) df_fma_acc(acc[c], zv, y[(size_t)c * TP + rr]);
   }
 }
+// Sketch of one sketch row over a tile: acc[c * d] += sum_t sign_t y[c][row_t] for CW
+// columns, entries in list order.  The sign is applied by flipping the sign bit: a
+// float64 negation would take a second slot of the (scarce) float64 pipe.
+template <int CW>
+__device__ __forceinline__ void sketch_row_f64(double* acc, int d, const double* y, int TP,
+                                               const uint8_t* e, int cnt) {
+  double v[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) v[c] = acc[(size_t)c * d];
+  for (int t = 0; t < cnt; ++t) {
+    const int ev = e[t];
+    const int r = ev >> 1;
+    const long long sg = (long long)(ev & 1) << 63;
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      v[c] += __longlong_as_double(__double_as_longlong(y[(size_t)c * TP + r]) ^ sg);
+  }
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[(size_t)c * d] = v[c];
+}
+// float32 values in the first 4 bytes of each 8-byte slot: y holds 2 floats per row
+template <int CW>
+__device__ __forceinline__ void sketch_row_f32(float* acc, int d, const float* y, int TP2,
+                                               const uint8_t* e, int cnt) {
+  float v[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) v[c] = acc[(size_t)c * d];
+  for (int t = 0; t < cnt; ++t) {
+    const int ev = e[t];
+    const int r = 2 * (ev >> 1);
+    const int sg = (ev & 1) << 31;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) v[c] += __int_as_float(__float_as_int(y[(size_t)c * TP2 + r]) ^ sg);
+  }
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[(size_t)c * d] = v[c];
+}
 #define RBO_CW_DISPATCH(fn, cw, ...)            \
   switch (cw) {                                 \
     case 8: fn<8>(__VA_ARGS__); break;          \
@@ -643,28 +680,17 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
         const int i = (int)(m & 0xFFFu), o = (int)((m >> 12) & 0x7FFu), cnt = (int)(m >> 23);
         const uint8_t* e = lst + o;
         if (MIXED) {
-          for (int c = 0; c < b; ++c) {
-            const float* yc = reinterpret_cast<const float*>(ys + (size_t)c * TP);
-            float v = skf[i + c * d];
-            for (int t = 0; t < cnt; ++t) {
-              const int ev = e[t];
-              // sign by flipping the sign bit (integer ALU, not a float negation)
-              v += __int_as_float(__float_as_int(yc[2 * (ev >> 1)]) ^ ((ev & 1) << 31));
-            }
-            skf[i + c * d] = v;
+          for (int c0 = 0; c0 < b; c0 += CB) {
+            const int cw = min(CB, b - c0);
+            RBO_CW_DISPATCH(sketch_row_f32, cw, skf + i + (size_t)c0 * d, d,
+                            reinterpret_cast<const float*>(ys + (size_t)c0 * TP), 2 * TP, e, cnt)
           }
         } else {
-          for (int c = 0; c < b; ++c) {
-            const double* yc = ys + (size_t)c * TP;
-            double v = skd[i + c * d];
-            for (int t = 0; t < cnt; ++t) {
-              const int ev = e[t];
-              // sign by flipping the sign bit: a float64 negation would take a
-              // second slot of the (scarce) float64 pipe
-              v += __longlong_as_double(__double_as_longlong(yc[ev >> 1]) ^
-                                        ((long long)(ev & 1) << 63));
-            }
-            skd[i + c * d] = v;
+          // up to CB columns at once: independent float64 add chains
+          for (int c0 = 0; c0 < b; c0 += CB) {
+            const int cw = min(CB, b - c0);
+            RBO_CW_DISPATCH(sketch_row_f64, cw, skd + i + (size_t)c0 * d, d, ys + (size_t)c0 * TP, TP,
+                            e, cnt)
           }
         }
       }

@@ -32,39 +32,6 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, int64_t nnz,
       if (status && sub == 0) set_error(status, RBO_ERR_ARG, 11);
       end = beg;
     }
-    if (LPR == 1) {
-      // one thread per row (short rows): the row's indices and values are loaded in
-      // groups of 8 ahead of the gathers, and no cross-lane reduction is needed (each
-      // float64 operation costs a slot of this GPU's narrow float64 pipe)
-      for (int j0 = beg; j0 < end; j0 += 8) {
-        int cj[8];
-        double vj[8], xj[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          cj[u] = -1;
-          vj[u] = 0.0;
-          if (j0 + u < end) {
-            cj[u] = __ldg(col + j0 + u);
-            vj[u] = __ldg(val + j0 + u);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          xj[u] = 0.0;
-          if (j0 + u < end) {
-            if (cj[u] < 0 || (int64_t)cj[u] >= n) {
-              if (status) set_error(status, RBO_ERR_ARG, 12);
-              cj[u] = -1;
-            } else {
-              xj[u] = dscale ? __ldg(dscale + cj[u]) * __ldg(x + cj[u]) : __ldg(x + cj[u]);
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (j0 + u < end && cj[u] >= 0) s = fma(vj[u], xj[u], s);
-      }
-    } else {
       for (int j = beg + sub; j < end; j += LPR) {
         const int cj = __ldg(col + j);
         if (cj < 0 || (int64_t)cj >= n) {
@@ -74,11 +41,100 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, int64_t nnz,
         const double xv = dscale ? __ldg(dscale + cj) * __ldg(x + cj) : __ldg(x + cj);
         s = fma(__ldg(val + j), xv, s);
       }
-    }
   }
 #pragma unroll
   for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LPR);
   if (row < n && sub == 0) y[row] = bvec ? (bvec[row] - s) : s;
+}
+
+
+// Short rows: each warp takes 32 consecutive rows.  The warp stages the entries of its
+// rows in chunks of SCH (coalesced index and value loads, the x gathers issued by the
+// same lanes), then every lane runs the multiply-adds of its own row from shared
+// memory, as two interleaved chains (even and odd entries) added at the end.  No
+// cross-lane float64 reduction is needed: each float64 operation costs a slot of this
+// GPU's narrow float64 pipe.
+constexpr int SCH = 256;
+__global__ void __launch_bounds__(256) spmv_stream_kernel(int64_t n, int64_t nnz,
+                                                          const int32_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col,
+                                                          const double* __restrict__ val,
+                                                          const double* __restrict__ dscale,
+                                                          const double* __restrict__ x,
+                                                          const double* __restrict__ bvec,
+                                                          double* __restrict__ y, DevStatus* status) {
+  __shared__ double sv[8][SCH], sx[8][SCH];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r0 = ((int64_t)blockIdx.x * 8 + warp) * 32;
+  if (r0 >= n) return;
+  const int64_t r = r0 + lane;
+  const int nr = (int)((n - r0) < 32 ? (n - r0) : 32);
+  int beg = 0, end = 0;
+  if (r < n) {
+    beg = __ldg(rowptr + r);
+    end = __ldg(rowptr + r + 1);
+  }
+  // the warp's entry range, from its first and last row
+  const int e0 = __shfl_sync(0xffffffffu, beg, 0);
+  const int e1 = __shfl_sync(0xffffffffu, end, nr - 1);
+  const bool range_ok = e0 >= 0 && e1 >= e0 && (int64_t)e1 <= nnz;
+  if (r < n && (!range_ok || beg < e0 || end < beg || end > e1)) {
+    if (status) set_error(status, RBO_ERR_ARG, 11);
+    end = beg;
+  }
+  double s = 0.0, s2 = 0.0;
+  if (range_ok) {
+    for (int c0 = e0; c0 < e1; c0 += SCH) {
+      const int cn = (e1 - c0) < SCH ? (e1 - c0) : SCH;
+      // all index and value loads first, then all gathers, then the stores: every
+      // load of a chunk is in flight at once
+      int cj[SCH / 32];
+      double v[SCH / 32], xv[SCH / 32];
+#pragma unroll
+      for (int u = 0; u < SCH / 32; ++u) {
+        const int t = u * 32 + lane;
+        cj[u] = -1;
+        v[u] = 0.0;
+        if (t < cn) {
+          cj[u] = __ldg(col + c0 + t);
+          v[u] = __ldg(val + c0 + t);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < SCH / 32; ++u) {
+        const int t = u * 32 + lane;
+        xv[u] = 0.0;
+        if (t < cn) {
+          if (cj[u] < 0 || (int64_t)cj[u] >= n) {
+            if (status) set_error(status, RBO_ERR_ARG, 12);
+            v[u] = 0.0;
+          } else {
+            xv[u] = dscale ? __ldg(dscale + cj[u]) * __ldg(x + cj[u]) : __ldg(x + cj[u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < SCH / 32; ++u) {
+        const int t = u * 32 + lane;
+        if (t < cn) {
+          sv[warp][t] = v[u];
+          sx[warp][t] = xv[u];
+        }
+      }
+      __syncwarp();
+      const int lo = beg > c0 ? beg : c0, hi = end < c0 + cn ? end : c0 + cn;
+      // two interleaved chains (entries of even and odd position in the row)
+      int e = lo;
+      for (; e + 1 < hi; e += 2) {
+        s = fma(sv[warp][e - c0], sx[warp][e - c0], s);
+        s2 = fma(sv[warp][e + 1 - c0], sx[warp][e + 1 - c0], s2);
+      }
+      if (e < hi) s = fma(sv[warp][e - c0], sx[warp][e - c0], s);
+      __syncwarp();
+    }
+  }
+  s += s2;
+  if (r < n) y[r] = bvec ? (bvec[r] - s) : s;
 }
 
 static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
@@ -109,9 +165,11 @@ static int spmv_dispatch(const CsrDev& A, const double* dscale, const double* x,
 static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
                                const double* b, double* y, DevStatus* status, cudaStream_t st) {
   const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
-  if (avg <= 12.0)
-    spmv_go<1>(A, dscale, x, b, y, status, st);
-  else if (avg <= 24.0)
+  if (avg <= 12.0) {
+    const int64_t blocks = (A.n + 255) / 256;
+    spmv_stream_kernel<<<(unsigned)blocks, 256, 0, st>>>(A.n, A.nnz, A.rowptr, A.col, A.val, dscale,
+                                                          x, b, y, status);
+  } else if (avg <= 24.0)
     spmv_go<8>(A, dscale, x, b, y, status, st);
   else
     spmv_go<32>(A, dscale, x, b, y, status, st);

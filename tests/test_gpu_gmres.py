@@ -35,6 +35,43 @@ def test_mpk_jacobi_scaled(rbo):
     assert np.allclose(V.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
 
 
+def _irregular_csr(seed):
+    """Short rows with empty rows, one row spanning several 256-entry chunks and a
+    row count that is not a multiple of 32."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    n = 1037
+    lens = rng.integers(0, 9, size=n)
+    lens[rng.choice(n, 40, replace=False)] = 0
+    lens[500], lens[31], lens[1036] = 700, 300, 12
+    rows = np.repeat(np.arange(n), lens)
+    cols = np.concatenate([rng.choice(n, k, replace=False) for k in lens])
+    A = sp.csr_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(n, n))
+    A.sort_indices()
+    return synth.CSR.from_scipy(A)
+
+
+def test_spmv_irregular_rows(rbo):
+    import torch
+    A = _irregular_csr(3)
+    assert 0 < A.nnz / A.n <= 12  # the short-row kernel
+    u = np.random.default_rng(2).standard_normal(A.n)
+    V = rbo.mpk_csr(rbo.DeviceCSR.from_host(A), torch.from_numpy(u).cuda(), 2)
+    ref = krylov.mpk(A.to_scipy(), u, 2)
+    got = V.cpu().numpy()
+    for i in range(2):
+        assert np.abs(got[:, i] - ref[:, i]).max() <= 1e-13 * np.abs(ref[:, i]).max()
+
+
+def test_spmv_column_out_of_range_is_reported(rbo):
+    import torch
+    A = _irregular_csr(4)
+    A.col[A.rowptr[500] + 3] = A.n + 5  # one bad index inside the long row
+    with pytest.raises(rbo.RboError) as e:
+        rbo.mpk_csr(rbo.DeviceCSR.from_host(A), torch.ones(A.n, dtype=torch.float64).cuda(), 1)
+    assert e.value.code == rbo.ERR_ARG
+
+
 @pytest.mark.parametrize("N,s,s_hat,m", [(16, 5, 0, 30), (16, 5, 10, 30), (20, 5, 20, 60),
                                          (12, 3, 0, 12)])
 def test_poisson_matches_oracle(rbo, N, s, s_hat, m):
