@@ -203,6 +203,7 @@ def run_ours(args):
 
     orth = run_orth(rbo, torch, args) if (rank == 0 and not args.no_orth) else None
     learned_res = run_learned(rbo, torch, args) if (rank == 0 and not args.no_learned) else None
+    stress_res = run_stress(rbo, torch, args) if (rank == 0 and args.stress) else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(A, b_host, last["one"]["iterations"])
@@ -232,6 +233,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "orth": orth,
             "learned": learned_res,
+            "stress": stress_res,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -269,7 +271,7 @@ def profile_steps(rbo, torch, step, barrier, args):
     rp = prof["rowpass"]
     avg_ms = rp["ms"] / max(rp["launches"], 1)
     achieved_flops = rp["flops"] / (rp["ms"] / 1e3) if rp["ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "rowpass_kernel<false> (fused FP64 row pass)",
+    roofline = {"bound": "alu", "kernel": "rowpass_kernel<0> (fused float64 row pass, all roles)",
                 "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_DERIVED / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_DERIVED,
                 "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 1.25 TFLOP/s nominal)",
@@ -452,6 +454,74 @@ def run_learned(rbo, torch, args):
             "infer_gbs_algorithmic": bytes_infer / (infer_ms / 1e3) / 1e9 if infer_ms else None}
 
 
+def run_stress(rbo, torch, args):
+    """Nonsymmetric 3D convection-diffusion, 7-point upwind, anisotropy (1, 1, 1e-3),
+    Peclet 100 (seed 7), N^3 cells; s-step GMRES(m=100, s=10) to 1e-10:
+    one-stage with CholQR2 (the deterministic baseline) for one cycle, then two-stage
+    RandBCGS2 (s_hat=50) in float64 and mixed precision with Jacobi and with the
+    learned SPAI (trained on smaller instances of the family; Jacobi fallback)."""
+    import numpy as np
+    import synth
+    from paper_2503_16717_gb300 import learned
+    N = args.stress_n
+    t0 = time.perf_counter()
+    Ah, meta = synth.convdiff3d_csr(N, seed=7)
+    A = rbo.DeviceCSR.from_host(Ah)
+    b = torch.from_numpy(synth.ones_rhs(Ah)).cuda()
+    t_gen = time.perf_counter() - t0
+    del Ah
+    out = {"N": N, "n": A.n, "nnz": A.nnz, "s": 10, "s_hat": 50, "m": 100, "tol": 1e-10,
+           "wind": meta["w"], "generate_s": t_gen, "max_restarts": args.stress_restarts}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    def row(info, sec, **kw):
+        d = {"status": info["status"], "converged": info["converged"],
+             "iterations": info["iterations"], "restarts": info["restarts"],
+             "relres": info["relres"], "s": sec}
+        if info["status"] != 0:
+            d["breakdown"] = {k: info.get(k) for k in ("breakdown_block", "breakdown_column",
+                                                       "breakdown_stage_name")}
+        d.update(kw)
+        return d
+
+    # the deterministic baseline: CholQR2 on the monomial panels (one cycle)
+    (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10, max_restarts=1,
+                                                   intra=rbo.INTRA_CHOLQR2))
+    out["cholqr2_one_cycle"] = row(info, sec)
+    # the learned SPAI, trained on the same family at 48^3
+    t0 = time.perf_counter()
+    train_set = learned.make_instances(lambda n_, sd: synth.convdiff3d_csr(n_, sd), range(100, 116), 48,
+                                       s=10, m=100)
+    net = rbo.GNN(seed=2)
+    hist = learned.train(net, train_set, epochs=8, lr=3e-3, lr_decay=0.8)
+    out["train"] = {"instances": 16, "grid": 48, "epoch_loss": hist["epoch_loss"],
+                    "s": time.perf_counter() - t0}
+    del train_set
+    jac = rbo.GNN(seed=0)
+    runs = []
+    for prec, pn in ((rbo.PREC_FP64, "fp64"), (rbo.PREC_MIXED, "mixed")):
+        (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, s_hat=50, m=100, tol=1e-10,
+                                                       precision=prec,
+                                                       max_restarts=args.stress_restarts))
+        runs.append(row(info, sec, precision=pn, precond="jacobi"))
+        (res, sec) = timed(lambda: learned.solve(net, A, b, jacobi=jac, s=10, s_hat=50, m=100,
+                                                 tol=1e-10, precision=prec,
+                                                 max_restarts=args.stress_restarts))
+        _, info, used = res
+        runs.append(row(info, sec, precision=pn, precond="learned" if used else "jacobi (fallback)",
+                        loss_learned=info["learned_loss"], loss_jacobi=info["jacobi_loss"]))
+    out["runs"] = runs
+    del A, b
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 def cpu_baseline(A, b, gpu_iterations, budget_cycles=2):
     """The oracle's one-stage s-step GMRES on the same problem for `budget_cycles`
@@ -526,6 +596,10 @@ def main():
     ap.add_argument("--no-df64", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-full", action="store_true")
+    ap.add_argument("--stress", action="store_true",
+                    help="also run the 3D convection-diffusion stress solve (s=10, s_hat=50, m=100)")
+    ap.add_argument("--stress-n", type=int, default=256, help="grid points per side of the stress case")
+    ap.add_argument("--stress-restarts", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

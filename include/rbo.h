@@ -74,7 +74,8 @@ typedef struct rbo_opts {
   int32_t precision;     /* RBO_PREC_*                                                  */
   int32_t v0;            /* 1: column 0 of V is the single start vector V_0 = [v_0]
                             (Table 1), normalised before the blocks                     */
-  int32_t intra;         /* RBO_INTRA_* (one-stage only)                                */
+  int32_t intra;         /* RBO_INTRA_*: one-stage only (block_orth_one_stage and the
+                            one-stage s-step GMRES); RBO_ERR_ARG for CHOLQR2 with s_hat > s */
   int32_t max_restarts;  /* GMRES: restart cycles allowed (default 1000 if <= 0)        */
   int32_t precond;       /* GMRES: 0 none, 1 Jacobi (M = diag(A), right preconditioner) */
   int32_t reserved[3];
@@ -109,6 +110,9 @@ typedef struct rbo_info {
   int64_t resid_ld;
   int32_t resid_cap;
   int32_t resid_len;         /* residual columns written                              */
+  int32_t fallbacks;         /* GMRES, RBO_PREC_MIXED: restart cycles redone in float64
+                                after a block lost orthogonality or broke down (float64
+                                then stays on for the rest of the solve)               */
 } rbo_info;
 
 /* ---- sparse-sign sketch (Section 3 / 5.2; the paper's Count sketch with zeta
@@ -219,6 +223,9 @@ int rbo_mpk_csr(const rbo_csr* A, const double* dscale, int32_t s, const double*
  * right preconditioner opts->precond.  x holds x0 on entry (resume from a
  * previous solve) and the solution on exit.  s_hat == 0 or s_hat == s: one-stage
  * randomized BCGS2; s < s_hat (s | s_hat | m): two-stage with RandBCGS2.
+ * opts->intra = RBO_INTRA_CHOLQR2 runs the one-stage scheme with CholQR2 instead of
+ * RandCholQR (the deterministic baseline, which breaks down on ill-conditioned
+ * monomial panels).
  * The sketch has d = 4 (m + 1) rows, zeta = 8, seed 42 unless `sk` is given.
  * Converged when ||b - A x||_2 <= tol ||b||_2 (true residual).
  * Errors: RBO_ERR_ARG, RBO_ERR_NOT_CONVERGED, RBO_ERR_CHOL_BREAKDOWN, RBO_ERR_CUDA,

@@ -62,7 +62,7 @@ class Info(C.Structure):
                 ("time_ms", C.c_double), ("history", C.POINTER(C.c_double)),
                 ("history_cap", C.c_int32), ("history_len", C.c_int32),
                 ("resid", C.c_void_p), ("resid_ld", C.c_int64), ("resid_cap", C.c_int32),
-                ("resid_len", C.c_int32)]
+                ("resid_len", C.c_int32), ("fallbacks", C.c_int32)]
 
 
 class Csr(C.Structure):
@@ -307,7 +307,7 @@ def mpk_csr(A: DeviceCSR, v0, s: int, V=None, dscale=None):
 def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int = 60,
                 tol: float = 1e-10, sk: Sketch | None = None, precision: int = PREC_FP64,
                 precond: int = 1, max_restarts: int = 0, history_cap: int = 4096,
-                M=None, resid=None, raise_on_error: bool = False):
+                M=None, resid=None, intra: int = INTRA_RANDCHOLQR, raise_on_error: bool = False):
     """s-step GMRES(m); returns (x, info).  s_hat in (0, s] -> one-stage, else two-stage.
     ``M``: optional device tensor of preconditioner values on A's pattern (right
     preconditioner; overrides ``precond``)."""
@@ -322,7 +322,7 @@ def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int =
     if resid is not None:
         pr, nrr, cap, ldr = _mat(resid, "resid")
         info.resid, info.resid_ld, info.resid_cap = pr.value, ldr, cap
-    o = _opts(precision, False, INTRA_RANDCHOLQR, max_restarts, precond)
+    o = _opts(precision, False, intra, max_restarts, precond)
     skh = sk.handle if sk is not None else None
     if M is not None:
         code = lib.rbo_sstep_gmres_precond(C.byref(st), _vec(M, "M"), _vec(b, "b"), _vec(x, "x"), s,

@@ -70,6 +70,8 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   // 0: none, 1: Jacobi (scaled copy of the values), 2: M on A's pattern (Mval)
   const int precond = Mval ? 2 : (opts ? (opts->precond ? 1 : 0) : 1);
   const int max_restarts = (opts && opts->max_restarts > 0) ? opts->max_restarts : 1000;
+  // first intra-block step of the one-stage scheme (the two-stage one is sketched)
+  const int intra = opts ? opts->intra : RBO_INTRA_RANDCHOLQR;
   const int ld = m + 1;
   const int64_t ldq = (n + 1) & ~int64_t(1);  // even: 16-byte aligned columns
 
@@ -152,8 +154,27 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   int its = 0;
   bool converged = false;
   double relres = INFINITY, est_rel = INFINITY;
-  int cycle = 0;
+  int cycle = 0, fallbacks = 0;
+  // Mixed precision: a block that the float32 sketch could not precondition (loss of
+  // orthogonality or a Cholesky breakdown) makes the restart cycle start over in
+  // float64, which stays on for the rest of the solve; x is only updated at the end of
+  // a cycle, so the cycle is simply redone.
+  auto fallback = [&](int code) -> bool {
+    if (!c.mixed || (code != RBO_ERR_LOST_ORTHOGONALITY && code != RBO_ERR_CHOL_BREAKDOWN))
+      return false;
+    if (cudaMemsetAsync(ar->status, 0, sizeof(DevStatus), st) != cudaSuccess) return false;
+    c.mixed = 0;
+    ++fallbacks;
+    if (info) {
+      info->breakdown_block = -1;
+      info->breakdown_column = -1;
+      info->breakdown_stage = 0;
+    }
+    return true;
+  };
   for (cycle = 0; cycle <= max_restarts; ++cycle) {
+    const int its0 = its;
+    const int resid_len0 = info ? info->resid_len : 0, hist_len0 = info ? info->history_len : 0;
     // r = b - Ahat y into basis column 0, q0 = r / ||r||
     if ((e = residual_launch(Araw, b, x, w.Qb, ar->status, st))) return e;
     if (info && info->resid && info->resid_len < info->resid_cap && info->resid_ld >= n) {
@@ -190,6 +211,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
     std::fill(Y.begin(), Y.end(), 0.0);
     int ncols = 1;
     int blk = 0;
+    bool redo = false;
     while (ncols < m + 1) {
       const int P = ncols;
       if (!two) {
@@ -197,14 +219,19 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
         const double* u = w.Qb + (int64_t)(P - 1) * ldq;
         for (int i = 0; i < s; ++i)
           if ((e = apply_op(i == 0 ? u : W + (int64_t)(i - 1) * ldq, W + (int64_t)i * ldq))) return e;
-        if ((e = one_stage_block(c, n, w.Qb, ldq, P, W, ldq, s, RBO_INTRA_RANDCHOLQR, w.Rdev, ld, P,
-                                 blk)))
+        if ((e = one_stage_block(c, n, w.Qb, ldq, P, W, ldq, s, intra, w.Rdev, ld, P, blk)))
           return e;
         if (cudaMemcpy2DAsync(Rh.data() + (size_t)P * ld, (size_t)ld * 8, w.Rdev + (size_t)P * ld,
                               (size_t)ld * 8, (size_t)(P + s) * 8, s, cudaMemcpyDeviceToHost,
                               st) != cudaSuccess)
           return RBO_ERR_CUDA;
-        if ((e = finish_status(ar, st, info))) return e;
+        if ((e = finish_status(ar, st, info))) {
+          if (fallback(e)) {
+            redo = true;
+            break;
+          }
+          return e;
+        }
         X[(P - 1) + (size_t)(P - 1) * m] = 1.0;
         for (int i = 1; i < s; ++i)
           for (int r = 0; r < P + i; ++r) X[r + (size_t)(P - 1 + i) * m] = Rh[r + (size_t)(P + i - 1) * ld];
@@ -240,7 +267,13 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
         if (cudaMemcpy2DAsync(coords.data(), (size_t)ld * 8, w.coords, (size_t)ld * 8,
                               (size_t)(P + K) * 8, K, cudaMemcpyDeviceToHost, st) != cudaSuccess)
           return RBO_ERR_CUDA;
-        if ((e = finish_status(ar, st, info))) return e;
+        if ((e = finish_status(ar, st, info))) {
+          if (fallback(e)) {
+            redo = true;
+            break;
+          }
+          return e;
+        }
         for (int j = 0; j < (int)gens.size(); ++j) {
           const int cc = P + j * s;  // first new column of panel j
           if (gens[j] < 0) {
@@ -272,6 +305,15 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
       est_rel = est / bnorm;
       if (est_rel <= tol) break;
     }
+    if (redo) {
+      its = its0;
+      if (info) {
+        info->resid_len = resid_len0;
+        info->history_len = hist_len0;
+      }
+      --cycle;
+      continue;
+    }
     // y += Q z
     const int k = ncols - 1;
     if (cudaMemcpyAsync(w.zdev, z.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -294,6 +336,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
     info->converged = converged ? 1 : 0;
     info->relres = relres;
     info->est_relres = est_rel;
+    info->fallbacks = fallbacks;
   }
   *launches_out = c.launches;
   return converged ? RBO_OK : RBO_ERR_NOT_CONVERGED;
@@ -335,6 +378,9 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   if (code == RBO_OK && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 &&
       opts->precision != RBO_PREC_MIXED && opts->precision != RBO_PREC_DF64)
+    code = RBO_ERR_ARG;
+  if (code == RBO_OK && opts && opts->intra != RBO_INTRA_RANDCHOLQR &&
+      (opts->intra != RBO_INTRA_CHOLQR2 || s_hat > s))
     code = RBO_ERR_ARG;
   int d = 4 * (m + 1), zeta = 8;
   uint64_t seed = 42;

@@ -143,3 +143,18 @@ def test_poisson_df64_matches_oracle(rbo, s_hat):
     assert info["converged"] == 1
     assert abs(info["iterations"] - ref.iterations) <= (s_hat or 5)
     assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6
+
+
+def test_mixed_precision_falls_back_to_float64_cycle(rbo):
+    # s = 10 monomial panels of a 3D convection-diffusion matrix: the float32 sketch
+    # cannot precondition some big panel, the cycle is redone in float64 and the
+    # solve converges with the float64 solve's iteration count
+    import torch
+    Ah, _ = synth.convdiff3d_csr(32, seed=7)
+    A = rbo.DeviceCSR.from_host(Ah)
+    b = torch.from_numpy(synth.ones_rhs(Ah)).cuda()
+    _, im = rbo.sstep_gmres(A, b, s=10, s_hat=50, m=100, tol=1e-10, precision=rbo.PREC_MIXED)
+    _, i64 = rbo.sstep_gmres(A, b, s=10, s_hat=50, m=100, tol=1e-10)
+    assert im["status"] == 0 and im["converged"] == 1 and im["relres"] <= 1e-10
+    assert im["fallbacks"] >= 1 and i64["fallbacks"] == 0
+    assert abs(im["iterations"] - i64["iterations"]) <= 50
