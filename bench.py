@@ -457,7 +457,7 @@ def run_learned(rbo, torch, args):
 def run_stress(rbo, torch, args):
     """Nonsymmetric 3D convection-diffusion, 7-point upwind, anisotropy (1, 1, 1e-3),
     Peclet 100 (seed 7), N^3 cells; s-step GMRES(m=100, s=10) to 1e-10:
-    one-stage with CholQR2 (the deterministic baseline) for one cycle, then two-stage
+    one-stage with CholQR2 (the deterministic baseline) and with RandCholQR, then two-stage
     RandBCGS2 (s_hat=50) in float64 and mixed precision with Jacobi and with the
     learned SPAI (trained on smaller instances of the family; Jacobi fallback)."""
     import numpy as np
@@ -483,17 +483,22 @@ def run_stress(rbo, torch, args):
     def row(info, sec, **kw):
         d = {"status": info["status"], "converged": info["converged"],
              "iterations": info["iterations"], "restarts": info["restarts"],
-             "relres": info["relres"], "s": sec}
+             "relres": info["relres"], "fallbacks": info["fallbacks"], "s": sec}
         if info["status"] != 0:
             d["breakdown"] = {k: info.get(k) for k in ("breakdown_block", "breakdown_column",
                                                        "breakdown_stage_name")}
         d.update(kw)
         return d
 
-    # the deterministic baseline: CholQR2 on the monomial panels (one cycle)
-    (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10, max_restarts=1,
+    # the deterministic baseline: one-stage with CholQR2 on the monomial panels
+    (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10,
+                                                   max_restarts=args.stress_restarts,
                                                    intra=rbo.INTRA_CHOLQR2))
-    out["cholqr2_one_cycle"] = row(info, sec)
+    out["cholqr2_one_stage"] = row(info, sec)
+    # the randomized one-stage scheme on the same panels
+    (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10,
+                                                   max_restarts=args.stress_restarts))
+    out["randcholqr_one_stage"] = row(info, sec)
     # the learned SPAI, trained on the same family at 48^3
     t0 = time.perf_counter()
     train_set = learned.make_instances(lambda n_, sd: synth.convdiff3d_csr(n_, sd), range(100, 116), 48,
