@@ -204,6 +204,7 @@ def run_ours(args):
     orth = run_orth(rbo, torch, args) if (rank == 0 and not args.no_orth) else None
     learned_res = run_learned(rbo, torch, args) if (rank == 0 and not args.no_learned) else None
     stress_res = run_stress(rbo, torch, args) if (rank == 0 and args.stress) else None
+    sweep_res = run_s_sweep(rbo, torch, Ad, bd, args) if (rank == 0 and args.s_sweep) else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(A, b_host, last["one"]["iterations"])
@@ -234,6 +235,7 @@ def run_ours(args):
             "orth": orth,
             "learned": learned_res,
             "stress": stress_res,
+            "s_sweep": sweep_res,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -454,6 +456,30 @@ def run_learned(rbo, torch, args):
             "infer_gbs_algorithmic": bytes_infer / (infer_ms / 1e3) / 1e9 if infer_ms else None}
 
 
+def run_s_sweep(rbo, torch, Ad, bd, args):
+    """Time to solution of the benchmark problem against the block size s (Sec. 8:
+    sketching keeps larger s stable): one-stage and two-stage (s_hat = the smallest
+    multiple of s that is >= 20 and divides m)."""
+    out = []
+    x = torch.zeros(Ad.n, dtype=torch.float64, device="cuda")
+    for s_ in (5, 10, 15, 20, 30):
+        sh = next(v for v in range(s_, M + 1, s_) if v >= 20 and M % v == 0)
+        for s_hat in (0, sh):
+            def go():
+                x.zero_()
+                return rbo.sstep_gmres(Ad, bd, x, s=s_, s_hat=s_hat, m=M, tol=TOL)[1]
+            go()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            info = go()
+            torch.cuda.synchronize()
+            out.append({"s": s_, "s_hat": s_hat or s_, "scheme": "two" if s_hat > s_ else "one",
+                        "status": info["status"], "iterations": info["iterations"],
+                        "restarts": info["restarts"], "relres": info["relres"],
+                        "s_per_solve": time.perf_counter() - t})
+    return out
+
+
 def run_stress(rbo, torch, args):
     """Nonsymmetric 3D convection-diffusion, 7-point upwind, anisotropy (1, 1, 1e-3),
     Peclet 100 (seed 7), N^3 cells; s-step GMRES(m=100, s=10) to 1e-10:
@@ -605,6 +631,8 @@ def main():
                     help="also run the 3D convection-diffusion stress solve (s=10, s_hat=50, m=100)")
     ap.add_argument("--stress-n", type=int, default=256, help="grid points per side of the stress case")
     ap.add_argument("--stress-restarts", type=int, default=100)
+    ap.add_argument("--s-sweep", action="store_true",
+                    help="also time the workload's solves for s in 5, 10, 15, 20, 30")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

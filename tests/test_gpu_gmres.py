@@ -73,7 +73,8 @@ def test_spmv_column_out_of_range_is_reported(rbo):
 
 
 @pytest.mark.parametrize("N,s,s_hat,m", [(16, 5, 0, 30), (16, 5, 10, 30), (20, 5, 20, 60),
-                                         (12, 3, 0, 12)])
+                                         (12, 3, 0, 12), (16, 10, 0, 60), (16, 15, 0, 30),
+                                         (16, 10, 30, 60)])
 def test_poisson_matches_oracle(rbo, N, s, s_hat, m):
     import torch
     A = synth.poisson3d_csr(N)
@@ -89,8 +90,10 @@ def test_poisson_matches_oracle(rbo, N, s, s_hat, m):
     r = b - A.to_scipy() @ xh
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
     assert np.abs(xh - 1.0).max() <= 1e-6
-    # restart histories agree while rounding has not diverged
-    h = dict(ref.history)
+    # restart histories agree while rounding has not diverged (with s > 5 the
+    # monomial panels are so ill-conditioned that the first cycle's residuals are
+    # decided by rounding)
+    h = dict(ref.history) if s <= 5 else {}
     for it, rel in info["history"][:3]:
         if it in h and h[it] > 1e-8:
             assert abs(rel - h[it]) <= 1e-6 * h[it]
@@ -158,3 +161,28 @@ def test_mixed_precision_falls_back_to_float64_cycle(rbo):
     assert im["status"] == 0 and im["converged"] == 1 and im["relres"] <= 1e-10
     assert im["fallbacks"] >= 1 and i64["fallbacks"] == 0
     assert abs(im["iterations"] - i64["iterations"]) <= 50
+
+
+@pytest.mark.parametrize("s", [5, 10])
+def test_cholqr2_intra_matches_oracle(rbo, s):
+    # the deterministic baseline inside GMRES (opts.intra): same iterations as the
+    # oracle's s-step GMRES with CholQR2, or both break down
+    import torch
+    A = synth.poisson3d_csr(14)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    x, info = rbo.sstep_gmres(Ad, torch.from_numpy(b).cuda(), s=s, m=30, tol=1e-10,
+                              intra=rbo.INTRA_CHOLQR2)
+    try:
+        ref = krylov.sstep_gmres(A, b, s=s, m=30, scheme="one", intra="cholqr2", tol=1e-10)
+        ref_ok = ref.converged
+    except Exception:
+        ref_ok = False
+    if info["status"] == 0:
+        assert ref_ok
+        assert abs(info["iterations"] - ref.iterations) <= s
+    else:
+        assert info["status"] in (rbo.ERR_CHOL_BREAKDOWN, rbo.ERR_LOST_ORTHOGONALITY)
+    with pytest.raises(rbo.RboError):
+        rbo.sstep_gmres(Ad, torch.from_numpy(b).cuda(), s=5, s_hat=10, m=30, tol=1e-10,
+                        intra=rbo.INTRA_CHOLQR2, raise_on_error=True)
