@@ -81,9 +81,10 @@ def _ls(H: np.ndarray, beta: float):
 def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None = None,
                 scheme: str = "one", intra: str = "rand", max_restarts: int = 200,
                 d: int | None = None, zeta: int = 8, seed: int = 42,
-                precond: str = "jacobi") -> GmresResult:
+                precond: str = "jacobi", preproc: str = "rand") -> GmresResult:
     """s-step GMRES(m) with one-stage (RandCholQR or CholQR2 BCGS2) or two-stage
-    (RandBCGS2, big panels of s_hat) block orthogonalization."""
+    (big panels of s_hat, preprocessed by RandBCGS2 or BCGS-PIP) block
+    orthogonalization."""
     if precond == "jacobi":
         Ahat, dinv = jacobi_scaled(A)
     else:
@@ -149,7 +150,7 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                     ncols += s
                     its += s
                 else:
-                    bp = TwoStageBigPanel(Qb[:, :P], sketch, s_hat)
+                    bp = TwoStageBigPanel(Qb[:, :P], sketch, s_hat, preproc)
                     gens = []
                     for j in range(s_hat // s):
                         if j == 0:

@@ -163,28 +163,48 @@ def sketched_bcgs2_hh(qs: np.ndarray, v: np.ndarray):
     return qn, c1 + c2, Tjj
 
 
+def bcgs_pip(Qbar: np.ndarray, Vh: np.ndarray):
+    """BCGS with the Pythagorean inner product (Section 7.1): one reduction of
+    [Qbar, Vh]^T Vh gives P = Qbar^T Vh and G = Vh^T Vh; the Pythagorean rule
+    replaces the Gram of the projected block by G - P^T P, whose Cholesky factor is
+    T_jj; then Qbar_j = (Vh - Qbar P) T_jj^{-1}.  With no earlier panel it is CholQR
+    (the section's footnote).  Returns (Qbar_j, T_col = P, T_jj)."""
+    P = Qbar.T @ Vh
+    G = Vh.T @ Vh
+    Tjj, info = cholesky_upper(G - P.T @ P)
+    if info >= 0:
+        raise Breakdown(info, where="bcgs-pip")
+    return solve_right_upper(Vh - Qbar @ P, Tjj), P, Tjj
+
+
 class TwoStageBigPanel:
     """State of one big panel of the two-stage scheme (Sections 6-7).
 
     Per panel j (``add_panel``):
       [C1_j, Vh_j] = BCGS(Q, V_j)                     (inter big-panel BCGS)
-      v_j = S Vh_j                                     (sketch)
-      [q_j, T_{<j,j}, T_jj] = sketched BCGS2-HH(qs, v_j)
-      Qbar_j = (Vh_j - Qbar_{<j} T_{<j,j}) T_jj^{-1}   (forward substitution,
+      preprocessing, preproc = "rand" (RandBCGS2, Section 7.2):
+        v_j = S Vh_j                                   (sketch)
+        [q_j, T_{<j,j}, T_jj] = sketched BCGS2-HH(qs, v_j)
+        Qbar_j = (Vh_j - Qbar_{<j} T_{<j,j}) T_jj^{-1} (forward substitution,
                                                        Appendix: Qbar = Vh T^{-1})
+      preproc = "pip" (BCGS-PIP, Section 7.1): [Qbar_j, T_{<j,j}, T_jj] =
+        BCGS-PIP(Qbar_{<j}, Vh_j)
     At the end (``finish``):
       [Qh_B, R'] = CholQR(Qbar_B);  [C2, Wt] = BCGS(Q, Qh_B);  [Q_B, R2] = CholQR(Wt)
       R_{Q,B} = C1 + C2 R' T,  R_BB = R2 R' T.
     ``coords_qbar`` = the coordinates of Qbar_B in [Q, Q_B]: [C2 R'; R2 R'].
     """
 
-    def __init__(self, Q: np.ndarray, sketch: Sketch, K: int):
+    def __init__(self, Q: np.ndarray, sketch: Sketch | None, K: int, preproc: str = "rand"):
+        if preproc not in ("rand", "pip"):
+            raise ValueError("preproc must be 'rand' or 'pip'")
         self.Q = Q
         self.sketch = sketch
+        self.preproc = preproc
         self.K = K
         n = Q.shape[0]
         self.Qbar = np.zeros((n, 0))
-        self.qs = np.zeros((sketch.d, 0))
+        self.qs = np.zeros((sketch.d if sketch is not None else 0, 0))
         self.T = np.zeros((K, K))
         self.C1 = np.zeros((Q.shape[1], K))
         self.cols = 0
@@ -194,6 +214,13 @@ class TwoStageBigPanel:
         a = self.cols
         C1, Vh = bcgs(self.Q, Vj)
         self.C1[:, a:a + k] = C1
+        if self.preproc == "pip":
+            Qbj, Tcol, Tjj = bcgs_pip(self.Qbar, Vh)
+            self.T[:a, a:a + k] = Tcol
+            self.T[a:a + k, a:a + k] = Tjj
+            self.Qbar = np.hstack([self.Qbar, Qbj])
+            self.cols += k
+            return Qbj
         v = self.sketch.apply(Vh)
         qn, Tcol, Tjj = sketched_bcgs2_hh(self.qs, v)
         self.T[:a, a:a + k] = Tcol
@@ -216,10 +243,11 @@ class TwoStageBigPanel:
         return QB, RQB, RBB, coords_qbar
 
 
-def block_orth_two_stage(V: np.ndarray, s: int, s_hat: int, sketch: Sketch,
-                         v0: bool = False) -> OrthResult:
-    """Two-stage block orthogonalization with RandBCGS2 preprocessing (flat form,
-    Figure 6 / Section 6): big panels of ``s_hat`` columns made of panels of ``s``."""
+def block_orth_two_stage(V: np.ndarray, s: int, s_hat: int, sketch: Sketch | None,
+                         v0: bool = False, preproc: str = "rand") -> OrthResult:
+    """Two-stage block orthogonalization (flat form, Figure 6 / Section 6): big panels
+    of ``s_hat`` columns made of panels of ``s``, preprocessed by RandBCGS2
+    (preproc="rand", Section 7.2) or BCGS-PIP (preproc="pip", Section 7.1)."""
     V = np.asarray(V, dtype=np.float64)
     n, c = V.shape
     Q, R, p = _start(V, v0)
@@ -227,7 +255,7 @@ def block_orth_two_stage(V: np.ndarray, s: int, s_hat: int, sketch: Sketch,
         raise ValueError("columns after v0 must be a multiple of s_hat, and s_hat of s")
     big = 0
     while p < c:
-        bp = TwoStageBigPanel(Q[:, :p], sketch, s_hat)
+        bp = TwoStageBigPanel(Q[:, :p], sketch, s_hat, preproc)
         try:
             for j in range(s_hat // s):
                 bp.add_panel(V[:, p + j * s:p + (j + 1) * s])

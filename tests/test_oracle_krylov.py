@@ -24,12 +24,14 @@ def test_spmv_and_mpk_match_dense(small):
     assert np.allclose(V[:, 3], np.linalg.matrix_power(D, 4) @ u, rtol=1e-12)
 
 
-@pytest.mark.parametrize("scheme,s_hat", [("one", None), ("two", 10), ("two", 20)])
-def test_sstep_estimates_equal_householder_gmres(scheme, s_hat):
+@pytest.mark.parametrize("scheme,s_hat,preproc", [("one", None, "rand"), ("two", 10, "rand"),
+                                                  ("two", 20, "rand"), ("two", 10, "pip")])
+def test_sstep_estimates_equal_householder_gmres(scheme, s_hat, preproc):
     A = synth.laplace2d_csr(20)
     b = synth.ones_rhs(A)
     ref = dict(krylov.householder_gmres(A, b, m=20, tol=1e-11, max_restarts=2).estimates)
-    g = krylov.sstep_gmres(A, b, s=5, m=20, s_hat=s_hat, scheme=scheme, tol=1e-11, max_restarts=2)
+    g = krylov.sstep_gmres(A, b, s=5, m=20, s_hat=s_hat, scheme=scheme, tol=1e-11, max_restarts=2,
+                           preproc=preproc)
     checked = 0
     for it, est in g.estimates:
         if it <= 40:

@@ -150,3 +150,64 @@ def test_mpk_laplace_basis_cholqr2_vs_rand():
         assert metrics.orth_error(Q) <= 1e-13
     assert first_fail is not None
     assert metrics.cond2(V[:, :first_fail + 1]) > 1e7
+
+
+# --- BCGS-PIP preprocessing (Section 7.1) -------------------------------------------
+def test_bcgs_pip_first_panel_is_cholqr():
+    # the section's footnote: with no earlier panel BCGS-PIP is CholQR
+    V = synth.glued_blocks(3000, 1, 5, 1e3, seed=5)
+    Qp, P, T = orth.bcgs_pip(np.zeros((3000, 0)), V)
+    Qc, Rc = orth.cholqr(V)
+    assert P.shape == (0, 5)
+    assert np.array_equal(T, Rc) and np.array_equal(Qp, Qc)
+
+
+def test_bcgs_pip_pythagorean_gram():
+    # with an orthonormal Qbar, G - P^T P is the Gram of the projected block, so
+    # T_jj^T T_jj = (Vh - Qbar P)^T (Vh - Qbar P) and Qbar_j is orthonormal and
+    # orthogonal to Qbar
+    rng = np.random.default_rng(3)
+    Qbar, _ = np.linalg.qr(rng.standard_normal((4000, 10)))
+    Vh = rng.standard_normal((4000, 5))
+    Qj, P, T = orth.bcgs_pip(Qbar, Vh)
+    W = Vh - Qbar @ (Qbar.T @ Vh)
+    assert np.allclose(T.T @ T, W.T @ W, rtol=1e-12, atol=1e-10)
+    assert np.allclose(P, Qbar.T @ Vh, rtol=0, atol=1e-12)
+    assert metrics.orth_error(np.hstack([Qbar, Qj])) <= 1e-13
+    assert np.allclose(Qj @ T + Qbar @ P, Vh, atol=1e-12)
+
+
+def test_two_stage_pip_matches_householder_reference(sk0):
+    V = synth.glued_blocks(N0, 12, 5, 1e4, seed=1, v0=True)
+    r = orth.block_orth_two_stage(V, 5, 30, None, v0=True, preproc="pip")
+    Qh, Rh = householder_qr(V, want_q=True)
+    assert r.ok
+    assert metrics.rel_diff(r.R, Rh) <= 1e-12
+    assert metrics.orth_error(r.Q) <= 1e-13
+    assert metrics.backward_error(V, r.Q, r.R) <= 1e-14
+
+
+def test_two_stage_pip_breaks_down_where_rand_does_not(sk0):
+    # Section 7.1: BCGS-PIP needs kappa(big panel)^2 eps < 1/2; RandBCGS2 only
+    # kappa eps < 1/2 (Proposition 7.2).  kappa = 1e10 big panels: PIP breaks down,
+    # the randomized preprocessing does not
+    V = synth.glued_blocks(N0, 12, 5, 1e10, seed=2)
+    pip = orth.block_orth_two_stage(V, 5, 30, None, preproc="pip")
+    rand = orth.block_orth_two_stage(V, 5, 30, sk0)
+    assert not pip.ok and pip.breakdown_where == "bcgs-pip"
+    assert rand.ok and metrics.orth_error(rand.Q) <= 1e-13
+    # below the threshold (kappa = 1e5, kappa^2 eps ~ 1e-6) PIP is O(eps)
+    V = synth.glued_blocks(N0, 12, 5, 1e5, seed=2)
+    pip = orth.block_orth_two_stage(V, 5, 30, None, preproc="pip")
+    assert pip.ok and metrics.orth_error(pip.Q) <= 1e-13
+
+
+def test_two_stage_pip_with_s_hat_equal_s_is_bcgs_cholqr():
+    # one panel per big panel: preprocessing is CholQR, then CholQR + BCGS + CholQR,
+    # i.e. BCGS2 with CholQR2 as the first intra-block step (same arithmetic)
+    V = synth.glued_blocks(N0, 6, 5, 1e3, seed=4)
+    a = orth.block_orth_two_stage(V, 5, 5, None, preproc="pip")
+    b = orth.block_orth_cholqr2(V, 5)
+    assert a.ok and b.ok
+    assert np.allclose(a.Q, b.Q, rtol=0, atol=1e-12)
+    assert metrics.rel_diff(a.R, b.R) <= 1e-12
