@@ -259,7 +259,7 @@ def profile_steps(rbo, torch, step, barrier, args):
     names = {1: "P1_gram", 2: "P2_update_sketch", 3: "P3_trsm_gram", 4: "P4_trsm_gram2",
              5: "P5_reorth_update_gram", 6: "P6_trsm", 7: "T1_gram", 8: "T2_update_sketch",
              9: "T3_forward_subst_gram", 10: "T4_trsm_gram2", 11: "T5_reorth_update_gram",
-             12: "T6_trsm", 13: "normalise", 0: "other"}
+             12: "T6_trsm", 13: "normalise", 14: "T2p_pip_gram", 0: "other"}
     passes = {}
     for tag, nm in names.items():
         r = rbo.profile_read(8 + tag)

@@ -78,7 +78,8 @@ typedef struct rbo_opts {
                             one-stage s-step GMRES); RBO_ERR_ARG for CHOLQR2 with s_hat > s */
   int32_t max_restarts;  /* GMRES: restart cycles allowed (default 1000 if <= 0)        */
   int32_t precond;       /* GMRES: 0 none, 1 Jacobi (M = diag(A), right preconditioner) */
-  int32_t reserved[3];
+  int32_t preproc;       /* two-stage: RBO_PREPROC_* (0 = RandBCGS2)                   */
+  int32_t reserved[2];
 } rbo_opts;
 
 #define RBO_STAGE_V0          1  /* normalisation of v_0                                  */
@@ -86,6 +87,12 @@ typedef struct rbo_opts {
 #define RBO_STAGE_INTRA2      3  /* second Cholesky of CholQR2                           */
 #define RBO_STAGE_FINAL       4  /* Cholesky after the re-orthogonalization              */
 #define RBO_STAGE_BIGPANEL    5  /* two-stage: CholQR of the preprocessed big panel      */
+#define RBO_STAGE_PREPROC     6  /* two-stage BCGS-PIP: Cholesky of the Pythagorean Gram */
+
+/* two-stage preprocessing of the panels of a big panel (rbo_opts.preproc) */
+#define RBO_PREPROC_RAND      0  /* RandBCGS2: sketch + sketched BCGS2-HH (Section 7.2)  */
+#define RBO_PREPROC_PIP       1  /* BCGS-PIP: one reduction of [Qbar V]^T V, Cholesky of
+                                    G - P^T P (Section 7.1); no sketch                   */
 
 typedef struct rbo_info {
   int32_t status;            /* same value as the return code                          */
@@ -219,6 +226,7 @@ int rbo_mpk_csr(const rbo_csr* A, const double* dscale, int32_t s, const double*
                 int64_t ldv, void* stream);
 
 /* ---- s-step GMRES (Section 4, Figure 1) -------------------------------------------
+ * (opts->preproc selects RandBCGS2 or BCGS-PIP for the two-stage panels)
  * Solves A x = b (b, x: device, n) with restart length m (s | m, m <= 128) and
  * right preconditioner opts->precond.  x holds x0 on entry (resume from a
  * previous solve) and the solution on exit.  s_hat == 0 or s_hat == s: one-stage

@@ -46,12 +46,15 @@ PREC_MIXED = 1
 PREC_DF64 = 2
 INTRA_RANDCHOLQR = 0
 INTRA_CHOLQR2 = 1
-STAGE_NAMES = {0: "", 1: "v0", 2: "intra", 3: "intra2", 4: "final", 5: "bigpanel"}
+STAGE_NAMES = {0: "", 1: "v0", 2: "intra", 3: "intra2", 4: "final", 5: "bigpanel", 6: "preproc"}
+PREPROC_RAND = 0
+PREPROC_PIP = 1
 
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("v0", C.c_int32), ("intra", C.c_int32),
-                ("max_restarts", C.c_int32), ("precond", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("max_restarts", C.c_int32), ("precond", C.c_int32), ("preproc", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class Info(C.Structure):
@@ -232,17 +235,20 @@ class OrthOut:
     info: dict
 
 
-def _opts(precision=PREC_FP64, v0=False, intra=INTRA_RANDCHOLQR, max_restarts=0, precond=1) -> Opts:
+def _opts(precision=PREC_FP64, v0=False, intra=INTRA_RANDCHOLQR, max_restarts=0, precond=1,
+          preproc=PREPROC_RAND) -> Opts:
     o = Opts()
     o.precision, o.v0, o.intra, o.max_restarts, o.precond = precision, int(v0), intra, max_restarts, precond
+    o.preproc = preproc
     return o
 
 
-def _orth_call(fn, args_pre, V, s_args, v0, precision, intra, where, raise_on_error):
+def _orth_call(fn, args_pre, V, s_args, v0, precision, intra, where, raise_on_error,
+               preproc=PREPROC_RAND):
     pv, n, c, ld = _mat(V, "V")
     R = np.zeros((c, c), dtype=np.float64)  # row-major storage of R^T == column-major R
     info = Info()
-    o = _opts(precision, v0, intra)
+    o = _opts(precision, v0, intra, preproc=preproc)
     code = fn(*args_pre, n, c, *s_args, pv, ld, R.ctypes.data_as(C.c_void_p), c, C.byref(o),
               C.byref(info), _stream())
     if code != OK and raise_on_error:
@@ -257,11 +263,14 @@ def block_orth_one_stage(sk: Sketch, V, s: int, v0: bool = False, precision: int
                       "block_orth_one_stage", raise_on_error)
 
 
-def block_orth_two_stage(sk: Sketch, V, s: int, s_hat: int, v0: bool = False,
-                         precision: int = PREC_FP64, raise_on_error: bool = True) -> OrthOut:
-    """Two-stage BCGS2 with RandBCGS2 preprocessing; V is overwritten by Q."""
-    return _orth_call(lib.rbo_block_orth_two_stage, (sk.handle,), V, (s, s_hat), v0, precision,
-                      INTRA_RANDCHOLQR, "block_orth_two_stage", raise_on_error)
+def block_orth_two_stage(sk: Sketch | None, V, s: int, s_hat: int, v0: bool = False,
+                         precision: int = PREC_FP64, raise_on_error: bool = True,
+                         preproc: int = PREPROC_RAND) -> OrthOut:
+    """Two-stage BCGS2 with RandBCGS2 (or BCGS-PIP: no sketch needed) preprocessing;
+    V is overwritten by Q."""
+    return _orth_call(lib.rbo_block_orth_two_stage, (sk.handle if sk is not None else None,), V,
+                      (s, s_hat), v0, precision, INTRA_RANDCHOLQR, "block_orth_two_stage",
+                      raise_on_error, preproc)
 
 
 def block_orth_cholqr2(V, s: int, v0: bool = False, raise_on_error: bool = True) -> OrthOut:
@@ -307,7 +316,8 @@ def mpk_csr(A: DeviceCSR, v0, s: int, V=None, dscale=None):
 def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int = 60,
                 tol: float = 1e-10, sk: Sketch | None = None, precision: int = PREC_FP64,
                 precond: int = 1, max_restarts: int = 0, history_cap: int = 4096,
-                M=None, resid=None, intra: int = INTRA_RANDCHOLQR, raise_on_error: bool = False):
+                M=None, resid=None, intra: int = INTRA_RANDCHOLQR, preproc: int = PREPROC_RAND,
+                raise_on_error: bool = False):
     """s-step GMRES(m); returns (x, info).  s_hat in (0, s] -> one-stage, else two-stage.
     ``M``: optional device tensor of preconditioner values on A's pattern (right
     preconditioner; overrides ``precond``)."""
@@ -322,7 +332,7 @@ def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int =
     if resid is not None:
         pr, nrr, cap, ldr = _mat(resid, "resid")
         info.resid, info.resid_ld, info.resid_cap = pr.value, ldr, cap
-    o = _opts(precision, False, intra, max_restarts, precond)
+    o = _opts(precision, False, intra, max_restarts, precond, preproc)
     skh = sk.handle if sk is not None else None
     if M is not None:
         code = lib.rbo_sstep_gmres_precond(C.byref(st), _vec(M, "M"), _vec(b, "b"), _vec(x, "x"), s,

@@ -304,7 +304,9 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   info_clear(info);
   int e = orth_common_checks(n, ncols, s, V, ldv, R, ldr, opts);
   if (e) return info_done(info, e, 0, t0);
-  const bool rand = scheme == 1 || intra == RBO_INTRA_RANDCHOLQR;
+  const int preproc = (scheme == 1 && opts) ? opts->preproc : RBO_PREPROC_RAND;
+  if (preproc != RBO_PREPROC_RAND && preproc != RBO_PREPROC_PIP) return info_done(info, RBO_ERR_ARG, 0, t0);
+  const bool rand = scheme == 1 ? preproc == RBO_PREPROC_RAND : intra == RBO_INTRA_RANDCHOLQR;
   if (rand && (!sk || n > sk->n_max)) return info_done(info, RBO_ERR_ARG, 0, t0);
   if (rand && (int64_t)sk->d * s > MAX_SKETCH_DK) return info_done(info, RBO_ERR_ARG, 0, t0);
   if (rand && sk->d < (scheme == 1 ? s_hat : s)) return info_done(info, RBO_ERR_ARG, 0, t0);
@@ -333,6 +335,7 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   c.st = st;
   c.mixed = (opts && opts->precision == RBO_PREC_MIXED) ? 1 : 0;
   c.df64 = (opts && opts->precision == RBO_PREC_DF64) ? 1 : 0;
+  c.pip = preproc == RBO_PREPROC_PIP ? 1 : 0;
   if (rand) {
     c.d = sk->d;
     c.zeta = sk->zeta;

@@ -104,7 +104,10 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   c.st = st;
   c.mixed = (opts && opts->precision == RBO_PREC_MIXED) ? 1 : 0;
   c.df64 = (opts && opts->precision == RBO_PREC_DF64) ? 1 : 0;
-  c.d = d;
+  c.pip = (two && opts && opts->preproc == RBO_PREPROC_PIP) ? 1 : 0;
+  // the sketch is only needed by RandCholQR (one-stage) and RandBCGS2 (two-stage)
+  const bool sketched = two ? !c.pip : intra == RBO_INTRA_RANDCHOLQR;
+  c.d = sketched ? d : 0;
   c.zeta = zeta;
   c.seed = seed;
   if ((e = orth_ctx_alloc(c, pmax, kmax, n))) return e;
@@ -374,8 +377,12 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   if (code == RBO_OK && (s_hat < s || s_hat % s != 0 || m % s_hat != 0 || s_hat > 64))
     code = RBO_ERR_ARG;
   if (code == RBO_OK && A->n < m + 1) code = RBO_ERR_ARG;
-  if (code == RBO_OK && (int64_t)(sk ? sk->d : 4 * (m + 1)) * s > MAX_SKETCH_DK) code = RBO_ERR_ARG;
-  if (code == RBO_OK && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
+  const bool pip = s_hat > s && opts && opts->preproc == RBO_PREPROC_PIP;
+  if (code == RBO_OK && opts && opts->preproc != RBO_PREPROC_RAND && opts->preproc != RBO_PREPROC_PIP)
+    code = RBO_ERR_ARG;
+  if (code == RBO_OK && !pip && (int64_t)(sk ? sk->d : 4 * (m + 1)) * s > MAX_SKETCH_DK)
+    code = RBO_ERR_ARG;
+  if (code == RBO_OK && !pip && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 &&
       opts->precision != RBO_PREC_MIXED && opts->precision != RBO_PREC_DF64)
     code = RBO_ERR_ARG;

@@ -208,7 +208,26 @@ int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
     r.epi.op = EPI_STORE; r.epi.out = c.C1; r.epi.out_ld = P; r.epi.col_off = cols;
     RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
   }
-  {
+  if (c.pip) {
+    // BCGS-PIP preprocessing (Section 7.1): Vh = V - Q C1, then one reduction of
+    // [Qbar_{<j}, Vh]^T Vh whose epilogue factors the Pythagorean Gram G - P^T P.
+    // The reduction stays float64 in every precision mode: its Cholesky loses
+    // kappa^2 of the accumulation precision.
+    if (P > 0) {
+      RowPass r;
+      r.df64 = c.df64; r.tag = 8;
+      r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
+      r.C = c.C1 + (size_t)cols * P; r.ldc = P; r.write_y = 1;
+      RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+    }
+    RowPass r;
+    r.tag = 14;
+    r.n = bp.n; r.X = bp.VB; r.ldx = bp.ldv; r.a = cols; r.Y = W; r.ldy = bp.ldv; r.b = k;
+    r.acc_x = cols > 0 ? 1 : 0; r.acc_y = 1;
+    r.epi.op = EPI_PIP; r.epi.T = c.T; r.epi.K = K; r.epi.poff = cols;
+    r.epi.stage = RBO_STAGE_PREPROC; r.epi.block = bp.blk;
+    RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
+  } else {
     RowPass r;
     r.df64 = c.df64; r.tag = 8;
     r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;

@@ -79,6 +79,8 @@ enum EpiOp : int {
   EPI_SKB2 = 4,       // two-stage: sketched BCGS2-HH against the stored sketched basis
   EPI_GB = 5,         // two-stage: store [X Y']^T Y' as block column of G_B; Cholesky at end
   EPI_STORE_ALL = 6,  // write all of Z (zr x b, ld zr) to out and the sketch (d x b) to out_sk
+  EPI_PIP = 7,        // two-stage BCGS-PIP: Z = [Qbar_{<j} Vh]^T Vh; T_jj = chol(G - P^T P);
+                      // T(0:poff, poff:poff+b) = P, T(poff:, poff:) = T_jj
 };
 
 enum AssembleOp : int {
@@ -204,6 +206,7 @@ struct OrthCtx {
   int mixed = 0;
   int df64 = 0;   // every pass in float32-pair arithmetic where it applies
   int d = 0, zeta = 0; uint64_t seed = 0;
+  int pip = 0;      // two-stage preprocessing by BCGS-PIP instead of RandBCGS2
   SketchSched sk;   // sketch schedule of the call's n rows
   // small device buffers, sized once per call by orth_ctx_alloc and reused by every
   // block (stream order makes the reuse safe)

@@ -181,6 +181,32 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
       assemble(e, G, b, sm + b * b, P.status);
       break;
     }
+    case EPI_PIP: {
+      // Pythagorean rule (Section 7.1): the Gram of Vh - Qbar P is G - P^T P
+      const int pp = ax, k = b, K = e.K, off = e.poff;
+      double* S = sm;  // k x k
+      for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        const int i = t % k, c = t / k;
+        double v = red[(pp + i) * b + c];
+        for (int l = 0; l < pp; ++l) v -= red[l * b + i] * red[l * b + c];
+        S[t] = v;
+      }
+      __syncthreads();
+      const int bad = cta_cholesky(S, k, s_flag);
+      if (bad >= 0) {
+        if (threadIdx.x == 0) set_breakdown(P.status, e.block, off + bad, e.stage);
+        return;
+      }
+      for (int t = threadIdx.x; t < pp * k; t += blockDim.x) {
+        const int l = t % pp, c = t / pp;
+        e.T[l + (size_t)(off + c) * K] = red[l * b + c];
+      }
+      for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        const int i = t % k, c = t / k;
+        e.T[(off + i) + (size_t)(off + c) * K] = (i <= c) ? S[t] : 0.0;
+      }
+      break;
+    }
     case EPI_HH: {
       const int d = rp.sk_d;
       double* A = sm;                      // d x b
@@ -854,6 +880,7 @@ static size_t epilogue_doubles(const RowPass& rp, int zr) {
     case EPI_HH: need = (size_t)d * b + (size_t)b * b + 2 * b + 64; break;
     case EPI_SKB2: need = (size_t)3 * d * b + (size_t)2 * e.poff * b + (size_t)b * b + 2 * b + 64; break;
     case EPI_GB: need = (size_t)(e.poff + b) * (e.poff + b) + 64; break;
+    case EPI_PIP: need = (size_t)b * b + 64; break;
     default: break;
   }
   (void)zr;

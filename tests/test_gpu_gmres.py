@@ -186,3 +186,18 @@ def test_cholqr2_intra_matches_oracle(rbo, s):
     with pytest.raises(rbo.RboError):
         rbo.sstep_gmres(Ad, torch.from_numpy(b).cuda(), s=5, s_hat=10, m=30, tol=1e-10,
                         intra=rbo.INTRA_CHOLQR2, raise_on_error=True)
+
+
+@pytest.mark.parametrize("N,s_hat", [(16, 10), (20, 10)])
+def test_two_stage_pip_gmres_matches_oracle(rbo, N, s_hat):
+    # (with s_hat = 20 the monomial big panels reach kappa ~ eps^{-1/2}, where
+    # whether the Pythagorean Cholesky breaks down is decided by rounding)
+    import torch
+    A = synth.poisson3d_csr(N)
+    b = synth.ones_rhs(A)
+    x, info = rbo.sstep_gmres(rbo.DeviceCSR.from_host(A), torch.from_numpy(b).cuda(), s=5,
+                              s_hat=s_hat, m=60, tol=1e-10, preproc=rbo.PREPROC_PIP)
+    ref = krylov.sstep_gmres(A, b, s=5, m=60, s_hat=s_hat, scheme="two", tol=1e-10, preproc="pip")
+    assert info["converged"] == 1 and ref.converged
+    assert abs(info["iterations"] - ref.iterations) <= s_hat
+    assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6

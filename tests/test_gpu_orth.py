@@ -192,3 +192,33 @@ def test_df64_ragged_sizes(rbo, n):
         assert out.info["status"] == 0
         assert metrics.orth_error(Q) <= 1e-13
         assert metrics.backward_error(V, Q, out.R) <= 1e-14
+
+
+# --- two-stage with BCGS-PIP preprocessing (Section 7.1) ---------------------------
+@pytest.mark.parametrize("n,s_hat", [(20000, 30), (12347, 10)])
+def test_two_stage_pip_matches_oracle(rbo, n, s_hat):
+    from gpu_util import to_dev, to_host
+    V = synth.glued_blocks(n, 12, 5, 1e4, seed=n + 3, v0=True)
+    Vd = to_dev(V)
+    out = rbo.block_orth_two_stage(None, Vd, 5, s_hat, v0=True, preproc=rbo.PREPROC_PIP)
+    Q = to_host(Vd)
+    ref = orth.block_orth_two_stage(V, 5, s_hat, None, v0=True, preproc="pip")
+    assert out.info["status"] == 0 and ref.ok
+    assert metrics.rel_diff(out.R, ref.R) <= 1e-12
+    assert np.abs(Q - ref.Q).max() <= 1e-9
+    assert metrics.orth_error(Q) <= 1e-13
+    assert metrics.backward_error(V, Q, out.R) <= 1e-14
+
+
+def test_two_stage_pip_breakdown_reported(rbo):
+    # kappa^2 eps >> 1: the Pythagorean Gram loses positive definiteness; both the
+    # oracle and the GPU report a breakdown in the preprocessing (RandBCGS2 does not)
+    from gpu_util import to_dev
+    V = synth.glued_blocks(20000, 12, 5, 1e10, seed=2)
+    out = rbo.block_orth_two_stage(None, to_dev(V), 5, 30, preproc=rbo.PREPROC_PIP,
+                                   raise_on_error=False)
+    ref = orth.block_orth_two_stage(V, 5, 30, None, preproc="pip")
+    assert not ref.ok and ref.breakdown_where == "bcgs-pip"
+    assert out.info["status"] == rbo.ERR_CHOL_BREAKDOWN
+    assert out.info["breakdown_stage_name"] == "preproc"
+    assert 0 <= out.info["breakdown_block"] < 2
