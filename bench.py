@@ -184,6 +184,23 @@ def run_ours(args):
                 "one_stage": {"iterations": i1["iterations"], "relres": i1["relres"]},
                 "two_stage": {"iterations": i2["iterations"], "relres": i2["relres"]}}
 
+    # the two-stage solve with BCGS-PIP preprocessing (the paper's deterministic
+    # two-stage comparator), same problem
+    def solve_pip():
+        x.zero_()
+        return rbo.sstep_gmres(Ad, bd, x, s=S, s_hat=S_HAT, m=M, tol=TOL,
+                               preproc=rbo.PREPROC_PIP)[1]
+    solve_pip()
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    ipip = solve_pip()
+    p1.record()
+    barrier()
+    pip = {"s_per_solve": p0.elapsed_time(p1) / 1e3, "status": ipip["status"],
+           "iterations": ipip["iterations"], "restarts": ipip["restarts"], "relres": ipip["relres"],
+           "breakdown_stage": ipip["breakdown_stage_name"]}
+
     # per-kernel times with CUDA events around each library launch (same steps again)
     if args.no_prof:
         prof, roofline, ms_prof = None, None, None
@@ -226,6 +243,7 @@ def run_ours(args):
                               "relres": two["relres"], "kernel_launches": two["kernel_launches"]},
             },
             "df64": df64,
+            "two_stage_pip": pip,
             "ms_per_step_profiled": ms_prof,
             "kernels": prof,
             "roofline": roofline,
@@ -241,6 +259,24 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def measured_traffic():
+    """DRAM bytes per row-pass launch from the committed ncu capture of this
+    workload (profiles/rowpass_traffic.json), or None when the kernel source has
+    changed since the counters were taken."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        with open(os.path.join(here, "profiles", "rowpass_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(here, "paper_2503_16717_gb300", "csrc", "rowpass.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if rec.get("rowpass_cu_sha256") != sha:
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def profile_steps(rbo, torch, step, barrier, args):
@@ -277,7 +313,7 @@ def profile_steps(rbo, torch, step, barrier, args):
                 "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_DERIVED / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_DERIVED,
                 "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 1.25 TFLOP/s nominal)",
-                "traffic": None, "launches": rp["launches"], "avg_launch_us": avg_ms * 1e3,
+                "traffic": measured_traffic(), "launches": rp["launches"], "avg_launch_us": avg_ms * 1e3,
                 "hbm_gbs_algorithmic": rp["bytes"] / (rp["ms"] / 1e3) / 1e9 if rp["ms"] > 0 else 0.0,
                 "share_of_step": rp["ms"] / args.steps / ms_prof if ms_prof > 0 else None}
 
@@ -336,8 +372,9 @@ def run_orth(rbo, torch, args):
             del V0
             torch.cuda.empty_cache()
             V0 = synth.glued_blocks_torch(n, nb, s, kappa, seed=1, v0=True, device="cuda")
-        for scheme in ("two", "one"):
-            for prec in (rbo.PREC_FP64, rbo.PREC_MIXED, rbo.PREC_DF64):
+        for scheme in ("two", "one", "two_pip"):
+            for prec in ((rbo.PREC_FP64,) if scheme == "two_pip" else
+                         (rbo.PREC_FP64, rbo.PREC_MIXED, rbo.PREC_DF64)):
                 Wm = W.t()  # n x c column-major view
                 times = []
                 info = None
@@ -349,6 +386,10 @@ def run_orth(rbo, torch, args):
                     if scheme == "two":
                         o = rbo.block_orth_two_stage(sk, Wm, s, s_hat, v0=True, precision=prec,
                                                      raise_on_error=False)
+                    elif scheme == "two_pip":
+                        o = rbo.block_orth_two_stage(None, Wm, s, s_hat, v0=True, precision=prec,
+                                                     raise_on_error=False,
+                                                     preproc=rbo.PREPROC_PIP)
                     else:
                         o = rbo.block_orth_one_stage(sk, Wm, s, v0=True, precision=prec,
                                                      raise_on_error=False)
@@ -364,6 +405,15 @@ def run_orth(rbo, torch, args):
                 k = s
                 if scheme == "one":
                     passes = 2 + sum(4 * p + 11 * k for p in range(1, c, k))
+                elif scheme == "two_pip":
+                    # per panel: C1 Gram (P+k), update (P+2k), PIP reduction (p'+k),
+                    # forward substitution (p'+2k); big-panel end as RandBCGS2
+                    passes = 2
+                    for P in range(1, c, s_hat):
+                        for j in range(s_hat // s):
+                            pp = j * k
+                            passes += (P + k) + (P + 2 * k) + (pp + k) + (pp + 2 * k)
+                        passes += (P + 2 * s_hat) + (P + 2 * s_hat) + 2 * s_hat
                 else:
                     passes = 2
                     for P in range(1, c, s_hat):
