@@ -112,3 +112,60 @@ class Sketch:
 
     def dense(self) -> np.ndarray:
         return self.S.toarray()
+
+
+# --- Gaussian and Count-Gauss sketches (Section 5.2) ---------------------------------
+# Gaussian entries from the SplitMix64 stream (written from the published
+# definitions, independently of the CUDA library):
+#   stream seed  seed_g = seed XOR GAUSS_SALT
+#   entry (k, r) of a Gaussian map with d rows uses output i = r * d + k + 1;
+#   u1 = (top 24 bits of h + 1/2) / 2^24 in (0, 1), u2 = (bits 16..39 of h) / 2^24;
+#   theta = sqrt(-2 ln u1) cos(2 pi u2) (Box and Muller 1958), rounded to float32
+#   (the CUDA side evaluates it in float32 arithmetic, within a few float32 ulps).
+GAUSS_SALT = 0x2545F4914F6CDD1D
+
+
+def gaussian_entries(seed: int, rows: np.ndarray, d: int) -> np.ndarray:
+    """theta[r, k] for the given rows r and k < d (len(rows) x d, float64 holding
+    float32 values)."""
+    rows = np.asarray(rows, dtype=np.uint64)
+    k = np.arange(d, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        i = rows[:, None] * np.uint64(d) + k[None, :] + np.uint64(1)
+    h = splitmix64_output(int(np.uint64(seed) ^ np.uint64(GAUSS_SALT)), i)
+    u1 = ((h >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24
+    u2 = ((h >> np.uint64(16)) & np.uint64(0xFFFFFF)).astype(np.float64) * 2.0 ** -24
+    g = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return g.astype(np.float32).astype(np.float64)
+
+
+class GaussianSketch:
+    """Dense Gaussian map S (d x n), entries N(0, 1) (unscaled, like the sparse
+    sign map: a scalar factor only rescales the sketch's R)."""
+
+    def __init__(self, n: int, d: int, seed: int):
+        self.n, self.d, self.seed = int(n), int(d), int(seed)
+        self.S = gaussian_entries(self.seed, np.arange(self.n), self.d).T.copy()
+
+    def apply(self, W: np.ndarray) -> np.ndarray:
+        return self.S @ np.asarray(W, dtype=np.float64)
+
+    def dense(self) -> np.ndarray:
+        return self.S
+
+
+class CountGaussSketch:
+    """S = G C (Section 5.2, Count-Gaussian): C is the d_inner x n Count sketch (one
+    +-1 per column: the sparse-sign map with zeta = 1 and the same seed), G the
+    d x d_inner Gaussian map whose entry (k, j) is gaussian_entries(seed, [j], d)[k]."""
+
+    def __init__(self, n: int, d: int, d_inner: int, seed: int):
+        self.n, self.d, self.d_inner, self.seed = int(n), int(d), int(d_inner), int(seed)
+        self.C = Sketch(self.n, self.d_inner, 1, self.seed)
+        self.G = gaussian_entries(self.seed, np.arange(self.d_inner), self.d).T.copy()
+
+    def apply(self, W: np.ndarray) -> np.ndarray:
+        return self.G @ self.C.apply(W)
+
+    def dense(self) -> np.ndarray:
+        return self.G @ self.C.dense()

@@ -211,3 +211,26 @@ def test_two_stage_pip_with_s_hat_equal_s_is_bcgs_cholqr():
     assert a.ok and b.ok
     assert np.allclose(a.Q, b.Q, rtol=0, atol=1e-12)
     assert metrics.rel_diff(a.R, b.R) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", ["gauss", "count_gauss"])
+def test_rand_schemes_with_gaussian_sketches(kind):
+    # Proposition 5.2 holds for any subspace embedding: RandCholQR with a Gaussian
+    # (d = 2s per block; 2 s_hat for the big panels) or Count-Gauss map keeps
+    # O(eps) orthogonality at kappa = 1e10 where CholQR2 fails, and the R factor
+    # is the unique one of the Householder reference
+    from oracle.sketch import CountGaussSketch, GaussianSketch
+    n = 20000
+    V = synth.glued_blocks(n, 12, 5, 1e10, seed=0)
+    mk = (lambda d: GaussianSketch(n, d, 42)) if kind == "gauss" else \
+         (lambda d: CountGaussSketch(n, d, 4 * d * d // 10, 42))
+    one = orth.block_orth_one_stage(V, 5, mk(10))
+    two = orth.block_orth_two_stage(V, 5, 30, mk(60))
+    for r in (one, two):
+        assert r.ok
+        assert metrics.orth_error(r.Q) <= 1e-13
+        assert metrics.backward_error(V, r.Q, r.R) <= 1e-14
+    W = synth.glued_blocks(n, 12, 5, 1e4, seed=1)
+    r = orth.block_orth_one_stage(W, 5, mk(10))
+    _, Rh = householder_qr(W, want_q=True)
+    assert metrics.rel_diff(r.R, Rh) <= 1e-12

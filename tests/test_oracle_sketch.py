@@ -97,3 +97,52 @@ def test_apply_matches_definition_on_unit_vectors():
 def test_too_small_d_is_an_error():
     with pytest.raises(SketchError):
         sparse_sign_entries(0, 10, 4, 8, 1)
+
+
+# --- Gaussian and Count-Gauss maps (Section 5.2) ------------------------------------
+def test_gaussian_entries_are_standard_normal():
+    from scipy import stats
+    from oracle.sketch import gaussian_entries
+    g = gaussian_entries(42, np.arange(40000), 25).ravel()
+    assert abs(g.mean()) < 5e-3 and abs(g.var() - 1.0) < 1e-2
+    assert stats.kstest(g, "norm").pvalue > 1e-3
+    # entries are float32 values, a function of (row, sketch row) only
+    assert np.array_equal(g.astype(np.float32).astype(np.float64), g)
+    sub = gaussian_entries(42, np.array([7, 123]), 25)
+    assert np.array_equal(sub, g.reshape(40000, 25)[[7, 123]])
+    # neighbouring sketch rows and neighbouring basis rows are uncorrelated draws
+    G = g.reshape(40000, 25)
+    assert abs(np.corrcoef(G[:, 3], G[:, 4])[0, 1]) < 0.02
+    assert abs(np.corrcoef(G[:-1, 0], G[1:, 0])[0, 1]) < 0.02
+
+
+@pytest.mark.parametrize("kind", ["gauss", "count_gauss"])
+def test_gaussian_maps_embed_subspaces(kind):
+    # Definition 3.1: a Gaussian map with d = O(k) rows, and the Count-Gauss map with
+    # a k^2 Count stage followed by O(k) Gaussian rows, keep a k-dimensional
+    # subspace well conditioned (mu < 1); the Gaussian map's mu shrinks as d grows
+    from oracle.sketch import CountGaussSketch, GaussianSketch
+    n, k = 20000, 10
+    U, _ = np.linalg.qr(np.random.default_rng(4).standard_normal((n, k)))
+    sk = GaussianSketch(n, 4 * k, 42) if kind == "gauss" else CountGaussSketch(n, 4 * k, k * k, 42)
+    sv = np.linalg.svd(sk.apply(U), compute_uv=False)
+    mu = (sv.max() ** 2 - sv.min() ** 2) / (sv.max() ** 2 + sv.min() ** 2)
+    assert mu < 0.9
+    if kind == "gauss":
+        sk4 = GaussianSketch(n, 16 * k, 42)
+        sv4 = np.linalg.svd(sk4.apply(U), compute_uv=False)
+        assert (sv4.max() ** 2 - sv4.min() ** 2) / (sv4.max() ** 2 + sv4.min() ** 2) < mu
+
+
+def test_count_gauss_is_gaussian_times_count():
+    # the Count stage is the zeta = 1 sparse-sign map with the same seed, the
+    # Gaussian stage the Gaussian entries over the inner rows
+    from oracle.sketch import CountGaussSketch, Sketch, gaussian_entries
+    n = 3000
+    cg = CountGaussSketch(n, 12, 40, 9)
+    C = Sketch(n, 40, 1, 9)
+    assert np.array_equal(cg.C.idx, C.idx) and np.array_equal(cg.C.sign, C.sign)
+    assert (np.abs(C.dense()).sum(axis=0) == 1).all()        # one +-1 per column
+    G = gaussian_entries(9, np.arange(40), 12).T
+    W = np.random.default_rng(1).standard_normal((n, 3))
+    assert np.allclose(cg.apply(W), G @ (C.dense() @ W), rtol=1e-13, atol=1e-12)
