@@ -89,6 +89,12 @@ typedef struct rbo_opts {
 #define RBO_STAGE_BIGPANEL    5  /* two-stage: CholQR of the preprocessed big panel      */
 #define RBO_STAGE_PREPROC     6  /* two-stage BCGS-PIP: Cholesky of the Pythagorean Gram */
 
+/* sketch types (rbo_sketch_create_ex; Section 5.2) */
+#define RBO_SKETCH_SPARSE_SIGN 0  /* zeta +-1 per column (zeta = 1: the Count sketch)     */
+#define RBO_SKETCH_GAUSSIAN    1  /* dense N(0, 1) entries, generated from the seed        */
+#define RBO_SKETCH_COUNT_GAUSS 2  /* Count sketch to d_inner rows, then a d x d_inner
+                                     Gaussian map                                        */
+
 /* two-stage preprocessing of the panels of a big panel (rbo_opts.preproc) */
 #define RBO_PREPROC_RAND      0  /* RandBCGS2: sketch + sketched BCGS2-HH (Section 7.2)  */
 #define RBO_PREPROC_PIP       1  /* BCGS-PIP: one reduction of [Qbar V]^T V, Cholesky of
@@ -128,19 +134,34 @@ typedef struct rbo_info {
  * from the SplitMix64 stream (Steele, Lea & Flood 2014) seeded with `seed`:
  * row r owns outputs i = 64 r + c + 1 (c = 0..63) of that stream; output h gives
  * index ((h >> 32) * d) >> 32 and sign -1 iff bit 0 of h is set; repeated
- * indices are skipped.  Nothing is stored: kernels recompute entries from
- * (seed, row).  Values are +-1, unscaled.                                         */
+ * indices are skipped.  The entries are hashed once per call (per GMRES solve)
+ * into a per-tile transposed schedule in the call's workspace.  Values are +-1,
+ * unscaled.                                                                        */
 typedef struct rbo_sketch_s* rbo_sketch;
 
 /* Create a sketch handle for matrices of up to n_max rows.  1 <= zeta <= d <= 4096.
  * The handle is library-owned (host memory only); destroy it with
  * rbo_sketch_destroy.  Errors: RBO_ERR_ARG.                                        */
 int rbo_sketch_create(int64_t n_max, int32_t d, int32_t zeta, uint64_t seed, rbo_sketch* out);
+/* Typed sketch (Section 5.2 compares these maps):
+ *  RBO_SKETCH_SPARSE_SIGN: as rbo_sketch_create (d_inner ignored).
+ *  RBO_SKETCH_GAUSSIAN: S (d x n) dense, S[k, r] = theta(seed, r, k, d) with theta =
+ *    sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller, float32 arithmetic) from output
+ *    i = r d + k + 1 of the SplitMix64 stream seeded with seed ^ 0x2545F4914F6CDD1D:
+ *    u1 = fl32(h>>40 + 1/2) 2^-24, u2 = ((h >> 16) & 0xFFFFFF) 2^-24.  Entries are
+ *    generated in the kernels, never stored.  1 <= d <= 256.
+ *  RBO_SKETCH_COUNT_GAUSS: S = G C with C the d_inner x n Count sketch (the
+ *    sparse-sign map with zeta = 1 and this seed) and G (d x d_inner) Gaussian with
+ *    G[k, j] = theta(seed, j, k, d).  1 <= d <= 4096, 1 <= d_inner <= 4096.
+ * zeta is used by SPARSE_SIGN only.  Errors: RBO_ERR_ARG, RBO_ERR_NOMEM.            */
+int rbo_sketch_create_ex(int64_t n_max, int32_t d, int32_t type, int32_t zeta, int32_t d_inner,
+                         uint64_t seed, rbo_sketch* out);
 int rbo_sketch_destroy(rbo_sketch sk);
 
 /* Materialise the entries of columns row0 .. row0+nrows-1 of S on the device, with
  * the same device code the sketch apply uses: idx (nrows x zeta, int32, row-major)
  * and sign (nrows x zeta, int8), both caller-owned device arrays.  For tests.
+ * Count-Gauss: the entries of its Count stage (zeta = 1); Gaussian: RBO_ERR_ARG.
  * Errors: RBO_ERR_ARG, RBO_ERR_SKETCH, RBO_ERR_CUDA.                               */
 int rbo_sketch_entries(rbo_sketch sk, int64_t row0, int64_t nrows, int32_t* idx, int8_t* sign,
                        void* stream);

@@ -49,6 +49,9 @@ INTRA_CHOLQR2 = 1
 STAGE_NAMES = {0: "", 1: "v0", 2: "intra", 3: "intra2", 4: "final", 5: "bigpanel", 6: "preproc"}
 PREPROC_RAND = 0
 PREPROC_PIP = 1
+SKETCH_SPARSE_SIGN = 0
+SKETCH_GAUSSIAN = 1
+SKETCH_COUNT_GAUSS = 2
 
 
 class Opts(C.Structure):
@@ -78,6 +81,7 @@ _vp, _i32, _i64, _u64, _dp = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_v
 # name -> (restype, argtypes)
 SIGNATURES = {
     "rbo_sketch_create": (C.c_int, [_i64, _i32, _i32, _u64, C.POINTER(_vp)]),
+    "rbo_sketch_create_ex": (C.c_int, [_i64, _i32, _i32, _i32, _i32, _u64, C.POINTER(_vp)]),
     "rbo_sketch_destroy": (C.c_int, [_vp]),
     "rbo_sketch_entries": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "rbo_sketch_apply": (C.c_int, [_vp, _i64, _i32, _vp, _i64, _dp, _i32, _vp]),
@@ -179,13 +183,17 @@ def info_dict(info: Info) -> dict:
 
 # ---- sketch ---------------------------------------------------------------------------------
 class Sketch:
-    """Handle of a sparse-sign sketch S (d x n_max, zeta entries +-1 per column)."""
+    """Handle of a sketch S (d x n_max): sparse-sign (zeta entries +-1 per column),
+    Gaussian, or Count-Gauss (a d_inner-row Count sketch followed by a Gaussian map)."""
 
-    def __init__(self, n_max: int, d: int, zeta: int = 8, seed: int = 42):
+    def __init__(self, n_max: int, d: int, zeta: int = 8, seed: int = 42,
+                 kind: int = SKETCH_SPARSE_SIGN, d_inner: int = 0):
         h = C.c_void_p()
-        _check(lib.rbo_sketch_create(n_max, d, zeta, seed, C.byref(h)), "sketch_create")
+        _check(lib.rbo_sketch_create_ex(n_max, d, kind, zeta, d_inner, seed, C.byref(h)),
+               "sketch_create")
         self.handle = h
-        self.n_max, self.d, self.zeta, self.seed = n_max, d, zeta, seed
+        self.n_max, self.d, self.seed, self.kind, self.d_inner = n_max, d, seed, kind, d_inner
+        self.zeta = zeta if kind == SKETCH_SPARSE_SIGN else 1
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -194,8 +202,9 @@ class Sketch:
             self.handle = None
 
 
-def sketch_create(n_max: int, d: int, zeta: int = 8, seed: int = 42) -> Sketch:
-    return Sketch(n_max, d, zeta, seed)
+def sketch_create(n_max: int, d: int, zeta: int = 8, seed: int = 42,
+                  kind: int = SKETCH_SPARSE_SIGN, d_inner: int = 0) -> Sketch:
+    return Sketch(n_max, d, zeta, seed, kind, d_inner)
 
 
 def sketch_entries(sk: Sketch, row0: int, nrows: int):

@@ -198,6 +198,34 @@ int rbo_sketch_create(int64_t n_max, int32_t d, int32_t zeta, uint64_t seed, rbo
   return RBO_OK;
 }
 
+int rbo_sketch_create_ex(int64_t n_max, int32_t d, int32_t type, int32_t zeta, int32_t d_inner,
+                         uint64_t seed, rbo_sketch* out) {
+  if (!out || n_max < 0 || d < 1) return RBO_ERR_ARG;
+  if (type == RBO_SKETCH_SPARSE_SIGN) {
+    if (d > 4096 || zeta < 1 || zeta > 16 || zeta > d) return RBO_ERR_ARG;
+    d_inner = 0;
+  } else if (type == RBO_SKETCH_GAUSSIAN) {
+    if (d > 256) return RBO_ERR_ARG;
+    zeta = 0;
+    d_inner = 0;
+  } else if (type == RBO_SKETCH_COUNT_GAUSS) {
+    if (d > 4096 || d_inner < 1 || d_inner > 4096) return RBO_ERR_ARG;
+    zeta = 1;
+  } else {
+    return RBO_ERR_ARG;
+  }
+  rbo_sketch s = new (std::nothrow) rbo_sketch_s;
+  if (!s) return RBO_ERR_NOMEM;
+  s->n_max = n_max;
+  s->d = d;
+  s->zeta = zeta;
+  s->seed = seed;
+  s->type = type;
+  s->d_inner = d_inner;
+  *out = s;
+  return RBO_OK;
+}
+
 int rbo_sketch_destroy(rbo_sketch sk) {
   delete sk;
   return RBO_OK;
@@ -206,13 +234,15 @@ int rbo_sketch_destroy(rbo_sketch sk) {
 int rbo_sketch_entries(rbo_sketch sk, int64_t row0, int64_t nrows, int32_t* idx, int8_t* sign,
                        void* stream) {
   if (!sk || row0 < 0 || nrows < 0 || (nrows > 0 && (!idx || !sign))) return RBO_ERR_ARG;
+  if (sk->type == RBO_SKETCH_GAUSSIAN) return RBO_ERR_ARG;
+  const int sd = sk->type == RBO_SKETCH_COUNT_GAUSS ? sk->d_inner : sk->d;
   int e = check_device();
   if (e) return e;
   cudaStream_t st = (cudaStream_t)stream;
   Arena* ar = nullptr;
   if ((e = arena_prepare(&ar, 0))) return e;
   if (cudaMemsetAsync(ar->base, 0, ARENA_HEADER, st) != cudaSuccess) return RBO_ERR_CUDA;
-  if ((e = sketch_entries_launch(row0, nrows, sk->d, sk->zeta, sk->seed, idx, sign, ar->status, st)))
+  if ((e = sketch_entries_launch(row0, nrows, sd, sk->zeta, sk->seed, idx, sign, ar->status, st)))
     return e;
   return finish_status(ar, st, nullptr);
 }
@@ -220,30 +250,32 @@ int rbo_sketch_entries(rbo_sketch sk, int64_t row0, int64_t nrows, int32_t* idx,
 int rbo_sketch_apply(rbo_sketch sk, int64_t n, int32_t k, const double* W, int64_t ldw, double* out,
                      int32_t precision, void* stream) {
   if (!sk || n < 1 || n > sk->n_max || k < 1 || k > 64 || !W || ldw < n || !out) return RBO_ERR_ARG;
-  if ((int64_t)sk->d * k > MAX_SKETCH_DK) return RBO_ERR_ARG;
+  if (!sketch_fits(sk, k)) return RBO_ERR_ARG;
   int e = check_device();
   if (e) return e;
   cudaStream_t st = (cudaStream_t)stream;
   Arena* ar = nullptr;
-  const int L = sk->d * k;
-  const int T = rowpass_sketch_T(0, k, sk->d, sk->zeta);
-  const size_t tab_bytes = sketch_sched_bytes(n, T, sk->d, sk->zeta);
-  if ((e = arena_prepare(&ar, reduction_bytes(L) + (size_t)L * 8 + tab_bytes + 2048))) return e;
+  const int dmax = std::max(sk->d, sk->d_inner);
+  const int L = orth_max_L(0, k, dmax);
+  const size_t bytes = reduction_bytes(L) + (size_t)sk->d * k * 8 +
+                       orth_ctx_bytes(0, k, sk->d, n, sk->zeta, sk->type, sk->d_inner) + 2048;
+  if ((e = arena_prepare(&ar, bytes))) return e;
   if ((e = arena_reserve_reduction(ar, L, st))) return e;
-  double* dout = (double*)ar->take((size_t)L * 8);
-  uint8_t* rec = (uint8_t*)ar->take(tab_bytes);
-  if (!dout || !rec) return RBO_ERR_NOMEM;
-  if ((e = sketch_sched_launch(n, T, sk->d, sk->zeta, sk->seed, rec, ar->status, st))) return e;
+  double* dout = (double*)ar->take((size_t)sk->d * k * 8);
+  if (!dout) return RBO_ERR_NOMEM;
+  OrthCtx c;
+  c.ar = ar;
+  c.st = st;
+  c.d = sk->d; c.zeta = sk->zeta; c.seed = sk->seed; c.sk_type = sk->type; c.d_inner = sk->d_inner;
+  if ((e = orth_ctx_alloc(c, 0, k, n))) return e;
   RowPass r;
   r.n = n; r.Y = const_cast<double*>(W); r.ldy = ldw; r.b = k;
-  r.sk_d = sk->d; r.sk_zeta = sk->zeta; r.sk_seed = sk->seed;
-  r.sk.rec = rec; r.sk.T = T; r.sk.mcap = sketch_sched_mcap(T, sk->d, sk->zeta);
-  r.sk.rec_bytes = sketch_sched_rec_bytes(T, sk->d, sk->zeta);
+  set_sketch(r, c);
   r.mixed = precision == RBO_PREC_MIXED ? 1 : 0;
-  r.epi.op = EPI_STORE_ALL; r.epi.out = dout; r.epi.out_sk = dout;
+  r.epi.op = EPI_SKETCH_OUT; r.epi.out_sk = dout;
   int launches = 0;
   if ((e = rowpass_launch(r, ar, st, &launches))) return e;
-  if (cudaMemcpyAsync(out, dout, (size_t)L * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (cudaMemcpyAsync(out, dout, (size_t)sk->d * k * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return RBO_ERR_CUDA;
   return finish_status(ar, st, nullptr);
 }
@@ -271,6 +303,7 @@ int rbo_gram(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, cons
     return RBO_ERR_CUDA;
   return finish_status(ar, st, nullptr);
 }
+
 
 static int orth_common_checks(int64_t n, int32_t ncols, int32_t s, double* V, int64_t ldv, double* R,
                               int64_t ldr, const rbo_opts* opts) {
@@ -308,7 +341,7 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   if (preproc != RBO_PREPROC_RAND && preproc != RBO_PREPROC_PIP) return info_done(info, RBO_ERR_ARG, 0, t0);
   const bool rand = scheme == 1 ? preproc == RBO_PREPROC_RAND : intra == RBO_INTRA_RANDCHOLQR;
   if (rand && (!sk || n > sk->n_max)) return info_done(info, RBO_ERR_ARG, 0, t0);
-  if (rand && (int64_t)sk->d * s > MAX_SKETCH_DK) return info_done(info, RBO_ERR_ARG, 0, t0);
+  if (rand && !sketch_fits(sk, s)) return info_done(info, RBO_ERR_ARG, 0, t0);
   if (rand && sk->d < (scheme == 1 ? s_hat : s)) return info_done(info, RBO_ERR_ARG, 0, t0);
   const int v0 = (opts && opts->v0) ? 1 : 0;
   if (scheme == 1) {
@@ -320,9 +353,11 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   const int d = rand ? sk->d : 0;
   const int kmax = scheme == 1 ? s_hat : s;
   const int pmax = ncols;
-  const int maxL = orth_max_L(pmax, kmax, d);
+  const int maxL = orth_max_L(pmax, kmax, rand ? std::max(sk->d, sk->d_inner) : 0);
   Arena* ar = nullptr;
-  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d, n, rand ? sk->zeta : 0) +
+  size_t bytes = reduction_bytes(maxL) +
+                 orth_ctx_bytes(pmax, kmax, d, n, rand ? sk->zeta : 0, rand ? sk->type : 0,
+                                rand ? sk->d_inner : 0) +
                  (size_t)ncols * ncols * 8 + 4096;
   if ((e = arena_prepare(&ar, bytes))) return info_done(info, e, 0, t0);
   if ((e = arena_reserve_reduction(ar, maxL, st))) return info_done(info, e, 0, t0);
@@ -340,6 +375,8 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
     c.d = sk->d;
     c.zeta = sk->zeta;
     c.seed = sk->seed;
+    c.sk_type = sk->type;
+    c.d_inner = sk->d_inner;
   }
   if ((e = orth_ctx_alloc(c, pmax, kmax, n))) return info_done(info, e, 0, t0);
   int p = 0;

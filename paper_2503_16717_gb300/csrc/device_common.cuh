@@ -65,6 +65,20 @@ __device__ __forceinline__ bool sketch_column(uint64_t seed, uint64_t row, int d
   return cnt == zeta;
 }
 
+// ---- Gaussian entries: SplitMix64 + Box-Muller ---------------------------------------
+// Entry (k, r) of a Gaussian map with d rows: output i = r d + k + 1 of the SplitMix64
+// stream seeded with seed ^ GAUSS_SALT; m1 = top 24 bits, u1 = fl32(m1 + 1/2) 2^-24 in
+// (0, 1), u2 = (bits 16..39) 2^-24; theta = sqrt(-2 ln u1) cos(2 pi u2) (Box and Muller
+// 1958) in float32 arithmetic.
+constexpr uint64_t GAUSS_SALT = 0x2545F4914F6CDD1DULL;
+__device__ __forceinline__ float gauss_entry(uint64_t seed, uint64_t r, int k, int d) {
+  const uint64_t h = splitmix_mix((seed ^ GAUSS_SALT) +
+                                  (r * (uint64_t)d + (uint64_t)k + 1ULL) * 0x9E3779B97F4A7C15ULL);
+  const float u1 = ((float)(uint32_t)(h >> 40) + 0.5f) * 0x1p-24f;
+  const float u2 = (float)(uint32_t)((h >> 16) & 0xFFFFFFULL) * 0x1p-24f;
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
 // ---- float64 -> float32 by integer operations ----------------------------------------
 // The f64->f32 conversion instruction runs on the float64 pipe of this GPU; this
 // version uses integer ALU only: round to nearest on the 29 dropped mantissa bits

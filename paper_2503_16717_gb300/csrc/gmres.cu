@@ -62,8 +62,9 @@ struct GmresWork {
 };
 
 int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, double* x, int s,
-                     int s_hat, int m, double tol, int d, int zeta, uint64_t seed,
-                     const rbo_opts* opts, rbo_info* info, cudaStream_t st, int* launches_out) {
+                     int s_hat, int m, double tol, int d, int zeta, uint64_t seed, int sk_type,
+                     int d_inner, const rbo_opts* opts, rbo_info* info, cudaStream_t st,
+                     int* launches_out) {
   const int64_t n = A->n;
   const bool two = s_hat > s;
   const int K = two ? s_hat : s;
@@ -76,8 +77,8 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   const int64_t ldq = (n + 1) & ~int64_t(1);  // even: 16-byte aligned columns
 
   const int pmax = m + 1, kmax = K;
-  const int maxL = std::max(orth_max_L(pmax, kmax, d), 1);
-  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d, n, zeta) +
+  const int maxL = std::max(orth_max_L(pmax, kmax, std::max(d, d_inner)), 1);
+  size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d, n, zeta, sk_type, d_inner) +
                  (size_t)ldq * (m + 1) * 8 + (size_t)A->nnz * 8 + 2 * (size_t)n * 8 +
                  (size_t)(m + 1) * (m + 1) * 8 + (size_t)(m + 1) * K * 8 + (size_t)m * 8 + 16 * 1024;
   Arena* ar = nullptr;
@@ -110,6 +111,8 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   c.d = sketched ? d : 0;
   c.zeta = zeta;
   c.seed = seed;
+  c.sk_type = sk_type;
+  c.d_inner = d_inner;
   if ((e = orth_ctx_alloc(c, pmax, kmax, n))) return e;
 
   CsrDev Araw{n, A->nnz, A->rowptr, A->col, A->val};
@@ -380,7 +383,8 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   const bool pip = s_hat > s && opts && opts->preproc == RBO_PREPROC_PIP;
   if (code == RBO_OK && opts && opts->preproc != RBO_PREPROC_RAND && opts->preproc != RBO_PREPROC_PIP)
     code = RBO_ERR_ARG;
-  if (code == RBO_OK && !pip && (int64_t)(sk ? sk->d : 4 * (m + 1)) * s > MAX_SKETCH_DK)
+  if (code == RBO_OK && !pip &&
+      (sk ? !sketch_fits(sk, s) : (int64_t)4 * (m + 1) * s > MAX_SKETCH_DK))
     code = RBO_ERR_ARG;
   if (code == RBO_OK && !pip && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 &&
@@ -389,13 +393,15 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   if (code == RBO_OK && opts && opts->intra != RBO_INTRA_RANDCHOLQR &&
       (opts->intra != RBO_INTRA_CHOLQR2 || s_hat > s))
     code = RBO_ERR_ARG;
-  int d = 4 * (m + 1), zeta = 8;
+  int d = 4 * (m + 1), zeta = 8, sk_type = RBO_SKETCH_SPARSE_SIGN, d_inner = 0;
   uint64_t seed = 42;
   if (sk) {
     if (sk->n_max < A->n) code = RBO_ERR_ARG;
     d = sk->d;
     zeta = sk->zeta;
     seed = sk->seed;
+    sk_type = sk->type;
+    d_inner = sk->d_inner;
   }
   if (code == RBO_OK) {
     int dev = 0, major = 0, minor = 0;
@@ -405,8 +411,8 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
     if (major != 10 || minor != 3) code = RBO_ERR_NO_DEVICE;
   }
   if (code == RBO_OK)
-    code = sstep_gmres_impl(A, Mval, b, x, s, s_hat, m, tol, d, zeta, seed, opts, info,
-                            (cudaStream_t)stream, &launches);
+    code = sstep_gmres_impl(A, Mval, b, x, s, s_hat, m, tol, d, zeta, seed, sk_type, d_inner, opts,
+                            info, (cudaStream_t)stream, &launches);
   if (info) {
     info->status = code;
     info->kernel_launches = launches;

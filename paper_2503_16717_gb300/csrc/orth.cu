@@ -19,16 +19,37 @@
 
 namespace rbo {
 
-size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta) {
+// The sparse part of a sketch that the row pass scatters (sparse-sign, or the Count
+// stage of Count-Gauss): rows and nonzeros per column; 0 rows for none.
+static void sched_shape(int type, int d, int d_inner, int zeta, int* ds, int* zs) {
+  *ds = type == RBO_SKETCH_SPARSE_SIGN ? d : (type == RBO_SKETCH_COUNT_GAUSS ? d_inner : 0);
+  *zs = type == RBO_SKETCH_SPARSE_SIGN ? zeta : 1;
+}
+
+size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta, int type, int d_inner) {
   size_t pk = (size_t)std::max(pmax, 1) * kmax, kk = (size_t)kmax * kmax;
   size_t dd = (size_t)std::max(d, 1) * kmax;
+  int ds = 0, zs = 0;
+  sched_shape(type, d, d_inner, zeta, &ds, &zs);
   const size_t tab =
-      d > 0 ? sketch_sched_bytes(n, rowpass_sketch_T(pmax, kmax, d, zeta), d, zeta) + 256 : 0;
+      (d > 0 && ds > 0) ? sketch_sched_bytes(n, rowpass_sketch_T(pmax, kmax, ds, zs), ds, zs) + 256 : 0;
   return (2 * pk + 6 * kk + dd + pk + kk) * 8 + 16 * 256 + tab;
 }
 
+void set_sketch(RowPass& r, const OrthCtx& c) {
+  r.sk_seed = c.seed;
+  if (c.sk_type == RBO_SKETCH_GAUSSIAN) {
+    r.sk_gd = c.d;
+  } else if (c.sk_type == RBO_SKETCH_COUNT_GAUSS) {
+    r.sk_d = c.d_inner; r.sk_zeta = 1; r.sk = c.sk; r.sk_cg = c.d;
+  } else {
+    r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk = c.sk;
+  }
+}
+
 int orth_max_L(int pmax, int kmax, int d) {
-  // Z of at most (pmax + kmax) x kmax plus a d x kmax sketch
+  // Z of at most (pmax + kmax) x kmax plus a d x kmax sketch (d: the largest of the
+  // final and the scattered sketch rows)
   return (pmax + kmax) * kmax + std::max(d, 0) * kmax;
 }
 
@@ -49,18 +70,20 @@ int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax, int64_t n) {
   if (!c.C1 || !c.C2 || !c.Rh || !c.Rp || !c.R2 || !c.T || !c.GB || !c.qs || !c.tmp)
     return RBO_ERR_NOMEM;
   c.sk = SketchSched();
-  if (c.d > 0) {
-    // the sketch is a fixed operator for the call: hashed and transposed once
-    const int T = rowpass_sketch_T(pmax, kmax, c.d, c.zeta);
-    uint8_t* rec = (uint8_t*)c.ar->take(sketch_sched_bytes(n, T, c.d, c.zeta));
+  int ds = 0, zs = 0;
+  sched_shape(c.sk_type, c.d, c.d_inner, c.zeta, &ds, &zs);
+  if (c.d > 0 && ds > 0) {
+    // the sparse sketch is a fixed operator for the call: hashed and transposed once
+    const int T = rowpass_sketch_T(pmax, kmax, ds, zs);
+    uint8_t* rec = (uint8_t*)c.ar->take(sketch_sched_bytes(n, T, ds, zs));
     if (!rec) return RBO_ERR_NOMEM;
-    const int e = sketch_sched_launch(n, T, c.d, c.zeta, c.seed, rec, c.ar->status, c.st);
+    const int e = sketch_sched_launch(n, T, ds, zs, c.seed, rec, c.ar->status, c.st);
     if (e != RBO_OK) return e;
     c.launches += 1;
     c.sk.rec = rec;
     c.sk.T = T;
-    c.sk.mcap = sketch_sched_mcap(T, c.d, c.zeta);
-    c.sk.rec_bytes = sketch_sched_rec_bytes(T, c.d, c.zeta);
+    c.sk.mcap = sketch_sched_mcap(T, ds, zs);
+    c.sk.rec_bytes = sketch_sched_rec_bytes(T, ds, zs);
   }
   return RBO_OK;
 }
@@ -124,7 +147,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
     r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
     if (p > 0) { r.C = c.C1; r.write_y = 1; }
     if (rand) {
-      r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed; r.sk = c.sk;
+      set_sketch(r, c);
       r.mixed = c.mixed;
       r.epi.op = EPI_HH; r.epi.out_r = c.Rh; r.epi.stage = RBO_STAGE_INTRA; r.epi.block = blk;
     } else {
@@ -232,7 +255,7 @@ int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
     r.df64 = c.df64; r.tag = 8;
     r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
     if (P > 0) { r.C = c.C1 + (size_t)cols * P; r.ldc = P; r.write_y = 1; }
-    r.sk_d = c.d; r.sk_zeta = c.zeta; r.sk_seed = c.seed; r.sk = c.sk;
+    set_sketch(r, c);
     r.mixed = c.mixed;
     r.epi.op = EPI_SKB2; r.epi.qs = c.qs; r.epi.T = c.T; r.epi.K = K; r.epi.poff = cols;
     r.epi.stage = RBO_STAGE_BIGPANEL; r.epi.block = bp.blk;

@@ -10,9 +10,11 @@
 // The sketch handle of the C ABI: parameters only, entries are recomputed.
 struct rbo_sketch_s {
   int64_t n_max;
-  int32_t d;
-  int32_t zeta;
+  int32_t d;        // rows of the sketch S W
+  int32_t zeta;     // sparse-sign: nonzeros per column (Count-Gauss: 1, in the Count stage)
   uint64_t seed;
+  int32_t type = 0;     // RBO_SKETCH_*
+  int32_t d_inner = 0;  // Count-Gauss: rows of the Count stage
 };
 
 namespace rbo {
@@ -20,6 +22,17 @@ namespace rbo {
 // Largest d * k (sketch rows x panel columns): the per-warp sketch partials of a row
 // pass live in shared memory.
 constexpr int64_t MAX_SKETCH_DK = 12288;
+
+// The sketch's shared-memory and Z-row limits for panels of up to kmax columns.
+inline bool sketch_fits(const ::rbo_sketch_s* sk, int kmax) {
+  switch (sk->type) {
+    case RBO_SKETCH_GAUSSIAN: return sk->d * kmax <= 8192;
+    case RBO_SKETCH_COUNT_GAUSS:
+      return (int64_t)sk->d_inner * kmax <= MAX_SKETCH_DK && (int64_t)sk->d * kmax <= MAX_SKETCH_DK;
+    default: return (int64_t)sk->d * kmax <= MAX_SKETCH_DK;
+  }
+}
+
 
 // Static scratch of rbo_gram_noalloc (see include/rbo.h).
 #define RBO_NOALLOC_SCRATCH_BYTES (4u << 20)
@@ -81,6 +94,7 @@ enum EpiOp : int {
   EPI_STORE_ALL = 6,  // write all of Z (zr x b, ld zr) to out and the sketch (d x b) to out_sk
   EPI_PIP = 7,        // two-stage BCGS-PIP: Z = [Qbar_{<j} Vh]^T Vh; T_jj = chol(G - P^T P);
                       // T(0:poff, poff:poff+b) = P, T(poff:, poff:) = T_jj
+  EPI_SKETCH_OUT = 8, // write the sketch S Y' (rows x b, column-major) to out_sk
 };
 
 enum AssembleOp : int {
@@ -135,8 +149,11 @@ struct RowPass {
   int write_y = 0;
   int acc_x = 0;                 // accumulate X^T Y'
   int acc_y = 0;                 // accumulate Y'^T Y'
-  int sk_d = 0, sk_zeta = 0; uint64_t sk_seed = 0;  // accumulate S Y' (d x b)
+  int sk_d = 0, sk_zeta = 0; uint64_t sk_seed = 0;  // accumulate S Y' (d x b), sparse-sign
   SketchSched sk;                // sketch schedule of the n rows (required with sk_d > 0)
+  int sk_gd = 0;                 // Gaussian sketch rows (entries generated per tile; Z rows)
+  int sk_cg = 0;                 // Count-Gauss: final rows (Gaussian stage in the epilogue;
+                                 // sk_d is then the Count stage, zeta 1)
   int mixed = 0;                 // float32 accumulation of X^T Y' and S Y'
   int df64 = 0;                  // float32-pair arithmetic for the Gram (and small projections)
   int small_coeffs = 0;          // C is a re-orthogonalization (O(eps kappa)) coefficient block
@@ -205,7 +222,8 @@ struct OrthCtx {
   int launches = 0;
   int mixed = 0;
   int df64 = 0;   // every pass in float32-pair arithmetic where it applies
-  int d = 0, zeta = 0; uint64_t seed = 0;
+  int d = 0, zeta = 0; uint64_t seed = 0;  // d: rows of the (final) sketch
+  int sk_type = 0, d_inner = 0;            // RBO_SKETCH_*; Count-Gauss Count-stage rows
   int pip = 0;      // two-stage preprocessing by BCGS-PIP instead of RandBCGS2
   SketchSched sk;   // sketch schedule of the call's n rows
   // small device buffers, sized once per call by orth_ctx_alloc and reused by every
@@ -220,7 +238,10 @@ struct OrthCtx {
 // With a sketch (c.d > 0) it also builds the sketch entry table of n rows.
 int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax, int64_t n);
 // Arena bytes orth_ctx_alloc will need.
-size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta);
+// (d: rows of the final sketch; type RBO_SKETCH_*; d_inner: Count-Gauss Count stage)
+size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta, int type, int d_inner);
+// Sketch fields of a row pass that applies the call's sketch.
+void set_sketch(RowPass& r, const OrthCtx& c);
 // Largest reduced-vector length of any pass for these sizes.
 int orth_max_L(int pmax, int kmax, int d);
 

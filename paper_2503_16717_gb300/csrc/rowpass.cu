@@ -53,6 +53,7 @@ struct PassDev {
   DevStatus* status;
   // shared memory layout (byte offsets from the dynamic base)
   int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_red;
+  int off_gth;            // Gaussian sketch entries of the tile (sk_gd x TP)
   int rec_off;            // sketch schedule record of the tile, offset inside a stage
 };
 
@@ -138,14 +139,42 @@ __device__ void assemble(const Epilogue& e, const double* R2, int k, double* scr
   __syncthreads();
 }
 
+// Rows of the sketch S Y' a pass produces (after the Count-Gauss Gaussian stage).
+__host__ __device__ inline int sketch_rows(const RowPass& rp) {
+  return rp.sk_gd > 0 ? rp.sk_gd : (rp.sk_cg > 0 ? rp.sk_cg : rp.sk_d);
+}
+
+// The reduced sketch S Y' (sketch_rows x b, column-major) into A: sparse-sign from
+// the scattered part of the partial; Gaussian from its Z rows; Count-Gauss as G times
+// the scattered Count stage, G generated here (float32 Box-Muller, as in the tiles).
+__device__ void load_sketch(const PassDev& P, const double* red, double* A) {
+  const RowPass& rp = P.p;
+  const int b = rp.b, d = sketch_rows(rp);
+  if (rp.sk_gd > 0) {
+    for (int t = threadIdx.x; t < d * b; t += blockDim.x) A[t] = red[(t % d) * b + t / d];
+  } else if (rp.sk_cg > 0) {
+    const int di = rp.sk_d;
+    for (int t = threadIdx.x; t < d * b; t += blockDim.x) {
+      const int k = t % d, c = t / d;
+      double s = 0.0;
+      for (int j = 0; j < di; ++j)
+        s = fma((double)gauss_entry(rp.sk_seed, (uint64_t)j, k, d), red[P.no + j + (size_t)c * di], s);
+      A[t] = s;
+    }
+  } else {
+    for (int t = threadIdx.x; t < d * b; t += blockDim.x) A[t] = red[P.no + t];
+  }
+  __syncthreads();
+}
+
 // The small dense work of the last CTA.  `red` holds the reduced partial
-// (Z: zr x b as o = i*b + c, then the sketch d x b column-major); `sm` is free
-// shared memory.
+// (Z: zr x b as o = i*b + c, then the scattered sketch d x b column-major); `sm` is
+// free shared memory.
 __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, int* s_flag) {
   const RowPass& rp = P.p;
   const Epilogue& e = rp.epi;
   const int b = rp.b;
-  const int ax = rp.acc_x ? rp.a : 0;
+  const int ax = rp.sk_gd + (rp.acc_x ? rp.a : 0);
   switch (e.op) {
     case EPI_STORE: {
       for (int t = threadIdx.x; t < ax * b; t += blockDim.x) {
@@ -207,15 +236,19 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
       }
       break;
     }
+    case EPI_SKETCH_OUT: {
+      load_sketch(P, red, sm);
+      for (int t = threadIdx.x; t < sketch_rows(rp) * b; t += blockDim.x) e.out_sk[t] = sm[t];
+      break;
+    }
     case EPI_HH: {
-      const int d = rp.sk_d;
+      const int d = sketch_rows(rp);
       double* A = sm;                      // d x b
       double* R = A + (size_t)d * b;       // b x b
       double* beta = R + b * b;            // b
       double* sg = beta + b;               // b
       double* scr = sg + b;                // 32
-      for (int t = threadIdx.x; t < d * b; t += blockDim.x) A[t] = red[P.no + t];
-      __syncthreads();
+      load_sketch(P, red, A);
       cta_householder(A, d, b, R, nullptr, beta, sg, scr);
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -227,7 +260,7 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
     }
     case EPI_SKB2: {
       // sketched BCGS2 with Householder intra step (Section 7.2)
-      const int d = rp.sk_d, k = b, pp = e.poff, K = e.K;
+      const int d = sketch_rows(rp), k = b, pp = e.poff, K = e.K;
       double* v = sm;                       // d x k
       double* A = v + (size_t)d * k;        // d x k (Householder work)
       double* Qn = A + (size_t)d * k;       // d x k
@@ -237,8 +270,7 @@ __device__ void run_epilogue(const PassDev& P, const double* red, double* sm, in
       double* beta = R + k * k;
       double* sg = beta + k;
       double* scr = sg + k;
-      for (int t = threadIdx.x; t < d * k; t += blockDim.x) v[t] = red[P.no + t];
-      __syncthreads();
+      load_sketch(P, red, v);
       if (pp > 0) {
         cta_gemm_tn(e.qs, d, v, d, pp, k, c1);
         cta_gemm_nn_sub(e.qs, d, c1, d, pp, k, v);
@@ -400,13 +432,16 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int T = P.T, TP = P.TP, a = rp.a, b = rp.b;
-  const int ax = rp.acc_x ? a : 0;
+  // Z rows: Gaussian sketch rows, then X rows (acc_x), then Y' rows (acc_y)
+  const int gd = rp.sk_gd;
+  const int ax = gd + (rp.acc_x ? a : 0);
   const int64_t n = rp.n;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   double* Cs = reinterpret_cast<double*>(smem + P.off_c);
   double* Ts = reinterpret_cast<double*>(smem + P.off_tri);
   double* dinv = reinterpret_cast<double*>(smem + P.off_dinv);
   double* skd = reinterpret_cast<double*>(smem + P.off_sk);
+  double* gth = reinterpret_cast<double*>(smem + P.off_gth);  // Gaussian sketch tile
   float* skf = reinterpret_cast<float*>(smem + P.off_sk);
   const int d = rp.sk_d;
   const bool do_sk = d > 0;
@@ -554,6 +589,20 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     };
     if (df_pre) to_pairs();
 
+    // Gaussian sketch entries of the tile's rows (float32 Box-Muller; zero past n),
+    // as extra Z rows of the Gram phase: S Y' = sum over rows of theta_r y'_r^T
+    if (gd > 0) {
+      for (int t = tid; t < gd * T; t += NT) {
+        const int r = t % T, k = t / T;
+        const float v = r < rows ? gauss_entry(rp.sk_seed, (uint64_t)(r0 + r), k, gd) : 0.0f;
+        if (MIXED)
+          reinterpret_cast<float*>(gth + (size_t)k * TP + r)[0] = v;
+        else
+          gth[(size_t)k * TP + r] = (double)v;
+      }
+      __syncthreads();
+    }
+
     // ---- phase A: y' = transform(y), in place in the Y stage --------------------
     // y' = y Tri^-1 by rows, in column blocks of CB: the block's update by the
     // finished columns runs over all (row, column) pairs, the substitution inside the
@@ -660,7 +709,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
           while (blk + 1 < P.nblk && item >= P.blk_start[blk + 1]) ++blk;
           const int i = item - P.blk_start[blk], c0 = min(blk * P.cw, b - P.cw);
           const int cw = P.cw;
-          const df* zsrc = reinterpret_cast<const df*>((i < ax) ? xs + (size_t)i * TP
+          const df* zsrc = reinterpret_cast<const df*>((i < ax) ? xs + (size_t)(i - gd) * TP
                                                                  : ys + (size_t)(i - ax) * TP);
           const df* ysrc = reinterpret_cast<const df*>(ys + (size_t)c0 * TP);
           RBO_CW_DISPATCH(gram_rows_df, cw, acci[k], zsrc, ysrc, g, T, P.tpo, TP)
@@ -680,7 +729,9 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
           while (blk + 1 < P.nblk && item >= P.blk_start[blk + 1]) ++blk;
           const int i = item - P.blk_start[blk], c0 = min(blk * P.cw, b - P.cw);
           const int cw = P.cw;
-          const double* zsrc = (i < ax) ? xs + (size_t)i * TP : ys + (size_t)(i - ax) * TP;
+          const double* zsrc = (i < gd)   ? gth + (size_t)i * TP
+                               : (i < ax) ? xs + (size_t)(i - gd) * TP
+                                          : ys + (size_t)(i - ax) * TP;
           const double* ysrc = ys + (size_t)c0 * TP;
           if (MIXED) {
             RBO_CW_DISPATCH(gram_rows_f32, cw, accf[k], zsrc, ysrc, g, T, P.tpo, TP)
@@ -872,7 +923,7 @@ static int occupancy(int smem) {
 
 // shared memory bytes of the small dense epilogue (beyond the reduced vector)
 static size_t epilogue_doubles(const RowPass& rp, int zr) {
-  const int b = rp.b, d = rp.sk_d;
+  const int b = rp.b, d = sketch_rows(rp);
   const Epilogue& e = rp.epi;
   size_t need = 0;
   switch (e.op) {
@@ -881,6 +932,7 @@ static size_t epilogue_doubles(const RowPass& rp, int zr) {
     case EPI_SKB2: need = (size_t)3 * d * b + (size_t)2 * e.poff * b + (size_t)b * b + 2 * b + 64; break;
     case EPI_GB: need = (size_t)(e.poff + b) * (e.poff + b) + 64; break;
     case EPI_PIP: need = (size_t)b * b + 64; break;
+    case EPI_SKETCH_OUT: need = (size_t)d * b + 64; break;
     default: break;
   }
   (void)zr;
@@ -893,7 +945,9 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   if (rp.a > 0 && rp.X == nullptr) return RBO_ERR_ARG;
   if (rp.a == 0) { rp.C = nullptr; rp.acc_x = 0; }
   if (rp.sk_d > DMAX || rp.sk_zeta > ZMAX) return RBO_ERR_ARG;
-  const int zr = (rp.acc_x ? rp.a : 0) + (rp.acc_y ? rp.b : 0);
+  if (rp.sk_gd < 0 || rp.sk_gd > 256 || rp.sk_cg < 0 || rp.sk_cg > DMAX) return RBO_ERR_ARG;
+  if (rp.sk_gd > 0 && rp.sk_d > 0) return RBO_ERR_ARG;
+  const int zr = rp.sk_gd + (rp.acc_x ? rp.a : 0) + (rp.acc_y ? rp.b : 0);
   const int no = zr * rp.b;
   if (no > 8192) return RBO_ERR_ARG;
   const int dsk = rp.sk_d > 0 ? rp.sk_d : 0;
@@ -902,7 +956,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   // Z columns in nblk blocks of one width cw <= CB (the last block starts at b - cw
   // and may overlap its neighbour): every Gram task has the same trip counts
   const int nblk = (rp.b + CB - 1) / CB, cw = (rp.b + nblk - 1) / nblk;
-  const int axr = rp.acc_x ? rp.a : 0;
+  const int axr = rp.sk_gd + (rp.acc_x ? rp.a : 0);
   int blk_start[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int k = 0; k < nblk; ++k) {
     const int c0 = std::min(k * cw, rp.b - cw);
@@ -915,7 +969,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   int arith = rp.mixed ? 1 : 0;
   if (rp.df64 && !rp.mixed) {
     const bool pre = !rp.Tri && rp.C && rp.small_coeffs;
-    const bool ok = (no > 0 || pre) && dsk == 0 && items <= 2 * NT;
+    const bool ok = (no > 0 || pre) && dsk == 0 && rp.sk_gd == 0 && items <= 2 * NT;
     arith = ok ? 2 : 0;
   }
   const int mixed = arith == 1 ? 1 : 0;
@@ -939,7 +993,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   size_t smem = 0;
   int tpo = 1, tasks = 0;
   size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_sk = 0,
-         rec_off = 0, off_red = 0;
+         rec_off = 0, off_red = 0, off_gth = 0;
   for (;;) {
     tpo = 1;
     if (items > 0)
@@ -956,6 +1010,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     o = (o + 15) & ~size_t(15);
     off_sk = o; o += (size_t)dsk * rp.b * (mixed ? 4 : 8);
     o = (o + 15) & ~size_t(15);
+    off_gth = o; o += (size_t)rp.sk_gd * TP * 8;
     size_t loop_bytes = o;
     size_t comb_bytes = off_stage + (size_t)tasks * CB * 8;
     off_red = 64;
@@ -1001,6 +1056,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.off_tri = (int)off_tri;
   P.off_dinv = (int)off_dinv;
   P.off_sk = (int)off_sk;
+  P.off_gth = (int)off_gth;
   P.rec_off = (int)rec_off;
   P.off_red = (int)off_red;
   P.partials = nullptr;
@@ -1034,6 +1090,7 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     if (rp.acc_x) fl += 2.0 * nn * A * B;                     // X^T Y'
     if (rp.acc_y) fl += nn * B * (B + 1.0);                   // Y'^T Y' (symmetric)
     if (rp.sk_d > 0) fl += nn * (double)rp.sk_zeta * B;       // sketch accumulation
+    if (rp.sk_gd > 0) fl += 2.0 * nn * rp.sk_gd * B;          // Gaussian sketch
     prof_stop(tok, st, 0, by, fl, rp.tag);
   }
   if (launches) ++*launches;

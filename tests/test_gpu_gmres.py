@@ -201,3 +201,22 @@ def test_two_stage_pip_gmres_matches_oracle(rbo, N, s_hat):
     assert info["converged"] == 1 and ref.converged
     assert abs(info["iterations"] - ref.iterations) <= s_hat
     assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6
+
+
+@pytest.mark.parametrize("kind", ["gauss", "count_gauss"])
+def test_gmres_with_gaussian_sketches(rbo, kind):
+    import torch
+    A = synth.poisson3d_csr(16)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    bd = torch.from_numpy(b).cuda()
+    if kind == "gauss":
+        sk = rbo.sketch_create(A.n, 2 * 21, seed=42, kind=rbo.SKETCH_GAUSSIAN)
+    else:
+        sk = rbo.sketch_create(A.n, 2 * 21, seed=42, kind=rbo.SKETCH_COUNT_GAUSS, d_inner=400)
+    for s_hat in (5, 20):
+        x, info = rbo.sstep_gmres(Ad, bd, s=5, s_hat=s_hat, m=60, tol=1e-10, sk=sk)
+        _, ref = rbo.sstep_gmres(Ad, bd, s=5, s_hat=s_hat, m=60, tol=1e-10)
+        assert info["converged"] == 1
+        assert abs(info["iterations"] - ref["iterations"]) <= s_hat
+        assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6

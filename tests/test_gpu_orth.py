@@ -222,3 +222,41 @@ def test_two_stage_pip_breakdown_reported(rbo):
     assert out.info["status"] == rbo.ERR_CHOL_BREAKDOWN
     assert out.info["breakdown_stage_name"] == "preproc"
     assert 0 <= out.info["breakdown_block"] < 2
+
+
+# --- Gaussian and Count-Gauss sketches in the randomized schemes (Section 5.2) ------
+@pytest.mark.parametrize("kind", ["gauss", "count_gauss"])
+def test_gaussian_sketch_schemes_match_oracle(rbo, kind):
+    from gpu_util import to_dev, to_host
+    from oracle.sketch import CountGaussSketch, GaussianSketch
+    n = 20000
+
+    def make(d):
+        if kind == "gauss":
+            return (rbo.sketch_create(n, d, seed=42, kind=rbo.SKETCH_GAUSSIAN),
+                    GaussianSketch(n, d, 42))
+        di = 4 * d * d // 10
+        return (rbo.sketch_create(n, d, seed=42, kind=rbo.SKETCH_COUNT_GAUSS, d_inner=di),
+                CountGaussSketch(n, d, di, 42))
+
+    # kappa = 1e4: R is unique, so the GPU and the oracle agree to rounding
+    V = synth.glued_blocks(n, 12, 5, 1e4, seed=1)
+    sk, osk = make(10)
+    Vd = to_dev(V)
+    out = rbo.block_orth_one_stage(sk, Vd, 5)
+    ref = orth.block_orth_one_stage(V, 5, osk)
+    assert out.info["status"] == 0 and ref.ok
+    assert metrics.rel_diff(out.R, ref.R) <= 1e-12
+    # kappa = 1e10 (CholQR2 fails): O(eps) with either map, one- and two-stage
+    V = synth.glued_blocks(n, 12, 5, 1e10, seed=0)
+    for scheme, d in (("one", 10), ("two", 60)):
+        sk, _ = make(d)
+        Vd = to_dev(V)
+        if scheme == "one":
+            out = rbo.block_orth_one_stage(sk, Vd, 5)
+        else:
+            out = rbo.block_orth_two_stage(sk, Vd, 5, 30)
+        Q = to_host(Vd)
+        assert out.info["status"] == 0
+        assert metrics.orth_error(Q) <= 1e-13
+        assert metrics.backward_error(V, Q, out.R) <= 1e-14

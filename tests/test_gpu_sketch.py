@@ -66,3 +66,47 @@ def test_apply_is_deterministic(rbo):
     a = rbo.sketch_apply(sk, W)
     b = rbo.sketch_apply(sk, W)
     assert np.array_equal(a, b)
+
+
+# --- Gaussian and Count-Gauss maps (Section 5.2) ------------------------------------
+def test_gaussian_entries_match_generator(rbo):
+    # S applied to the unit vectors e_0..e_{n-1} returns S's columns: the GPU's
+    # float32 Box-Muller values agree with the oracle's float32-rounded float64
+    # evaluation of the same SplitMix64 draws to a few float32 ulps
+    import torch
+    from oracle.sketch import gaussian_entries
+    n, d = 64, 40
+    sk = rbo.sketch_create(n, d, seed=11, kind=rbo.SKETCH_GAUSSIAN)
+    Wd = rbo.colmajor(n, n)
+    Wd.copy_(torch.eye(n, dtype=torch.float64))
+    got = rbo.sketch_apply(sk, Wd)                       # d x n
+    ref = gaussian_entries(11, np.arange(n), d).T
+    assert np.abs(got - ref).max() <= 8 * 2.0 ** -23 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kind", ["gauss", "count_gauss"])
+@pytest.mark.parametrize("n,k", [(20000, 5), (12345, 11), (65, 3)])
+def test_gaussian_maps_apply(rbo, kind, n, k):
+    from gpu_util import to_dev
+    from oracle.sketch import CountGaussSketch, GaussianSketch
+    W = np.random.default_rng(n + k).standard_normal((n, k))
+    if kind == "gauss":
+        sk = rbo.sketch_create(n, 2 * k + 2, seed=5, kind=rbo.SKETCH_GAUSSIAN)
+        ref = GaussianSketch(n, 2 * k + 2, 5).apply(W)
+    else:
+        sk = rbo.sketch_create(n, 2 * k + 2, seed=5, kind=rbo.SKETCH_COUNT_GAUSS, d_inner=k * k + 4)
+        ref = CountGaussSketch(n, 2 * k + 2, k * k + 4, 5).apply(W)
+    got = rbo.sketch_apply(sk, to_dev(W))
+    # entries of S differ from the oracle's by float32 ulps; sums of n terms
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+    if kind == "count_gauss":
+        idx, sgn = rbo.sketch_entries(sk, 0, n)
+        ref_idx, ref_sgn = sparse_sign_entries(0, n, k * k + 4, 1, 5)
+        assert np.array_equal(idx.cpu().numpy(), ref_idx)
+        assert np.array_equal(sgn.cpu().numpy(), ref_sgn)
+
+
+def test_gaussian_sketch_is_rejected_by_entries(rbo):
+    sk = rbo.sketch_create(100, 10, seed=1, kind=rbo.SKETCH_GAUSSIAN)
+    with pytest.raises(rbo.RboError):
+        rbo.sketch_entries(sk, 0, 10)
