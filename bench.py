@@ -428,9 +428,39 @@ def run_orth(rbo, torch, args):
                             "status": info["status"], "ms": ms, "cols_per_s": c / (ms / 1e3),
                             "hbm_gbs_algorithmic": gb / (ms / 1e3), "orth_err": oe,
                             "launches": info["kernel_launches"]})
+    # sketch types (Section 5.2): the same orthogonalizations (kappa of the last
+    # sweep entry) with the Gaussian, Count and Count-Gauss maps
+    kinds = [("sparse_sign", dict(d=4 * c, zeta=8)),
+             ("count", dict(d=4 * c, zeta=1)),
+             ("gaussian", dict(d=2 * s_hat, kind=rbo.SKETCH_GAUSSIAN)),
+             ("count_gauss", dict(d=2 * s_hat, kind=rbo.SKETCH_COUNT_GAUSS, d_inner=4 * c))]
+    types = []
+    for name, kw in kinds:
+        skt = rbo.sketch_create(n, kw.pop("d"), seed=42, **kw)
+        for scheme in ("one", "two"):
+            Wm = W.t()
+            times = []
+            for rep_ in range(3):
+                W.copy_(V0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if scheme == "two":
+                    o = rbo.block_orth_two_stage(skt, Wm, s, s_hat, v0=True, raise_on_error=False)
+                else:
+                    o = rbo.block_orth_one_stage(skt, Wm, s, v0=True, raise_on_error=False)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep_ > 0:
+                    times.append(e0.elapsed_time(e1))
+            G = rbo.gram(Wm, Wm)
+            oe = float(np.max(np.abs(np.linalg.eigvalsh(np.eye(c) - 0.5 * (G + G.T)))))
+            types.append({"sketch": name, "d": skt.d, "scheme": scheme, "kappa": kappas[-1],
+                          "status": o.info["status"], "ms": min(times), "orth_err": oe})
     del V0, W
     torch.cuda.empty_cache()
-    return {"n": n, "cols": c, "s": s, "s_hat": s_hat, "d": 4 * c, "results": out}
+    return {"n": n, "cols": c, "s": s, "s_hat": s_hat, "d": 4 * c, "results": out,
+            "sketch_types": types}
 
 
 def run_learned(rbo, torch, args):
