@@ -49,6 +49,73 @@ def mpk(Ahat, u: np.ndarray, s: int) -> np.ndarray:
     return V
 
 
+# --- Newton basis (Section 4 mentions it as the MPK option of Trilinos; Bai, Hu and
+# Reichel, IMA J. Numer. Anal. 14, 1994) ------------------------------------------
+def leja_order(theta: np.ndarray, rtol: float = 1e-12) -> list:
+    """Modified Leja ordering of the Ritz values ``theta``: the first point has the
+    largest modulus, every next point maximises the product of its distances to the
+    points already chosen (sum of logarithms), and a complex point is followed at once
+    by its conjugate.  Values whose imaginary part is below rtol*|value| count as real."""
+    theta = np.asarray(theta, dtype=np.complex128)
+    scale = max(float(np.abs(theta).max()), 1e-300) if theta.size else 1.0
+    cand = []
+    for z in theta:
+        if abs(z.imag) <= rtol * scale:
+            cand.append(complex(z.real, 0.0))
+        elif z.imag > 0:
+            cand.append(complex(z))
+    out = []
+    while cand:
+        if not out:
+            j = int(np.argmax([abs(z) for z in cand]))
+        else:
+            def score(z):
+                return sum(np.log(max(abs(z - w), 1e-300 * scale)) for w in out)
+            j = int(np.argmax([score(z) for z in cand]))
+        z = cand.pop(j)
+        out.append(z)
+        if z.imag != 0.0:
+            out.append(z.conjugate())
+    return out
+
+
+def newton_shifts(H: np.ndarray, s: int):
+    """Shifts for s Newton-basis vectors from the square upper-Hessenberg H (the
+    last cycle's Arnoldi matrix): the first s of the Ritz values in Leja order, as
+    the real recurrence v_{i+1} = (Ahat - alpha_i) v_i + beta_i v_{i-1}, with
+    alpha_i = Re theta_i and beta_i = (Im theta_i)^2 for the second value of a
+    conjugate pair (0 otherwise).  A pair split by the s-th position contributes
+    its real part only."""
+    order = leja_order(np.linalg.eigvals(H))
+    alpha, beta = np.zeros(s), np.zeros(s)
+    i = 0
+    while i < s and i < len(order):
+        z = order[i]
+        alpha[i] = z.real
+        if z.imag > 0 and i + 1 < s:
+            alpha[i + 1] = z.real
+            beta[i + 1] = z.imag ** 2
+            i += 2
+        else:
+            i += 1
+    return alpha, beta
+
+
+def mpk_newton(Ahat, u: np.ndarray, alpha: np.ndarray, beta: np.ndarray) -> np.ndarray:
+    """Newton matrix-powers kernel: v_0 = u, v_{i+1} = (Ahat - alpha_i) v_i + beta_i v_{i-1}
+    (beta_0 = 0); returns [v_1, ..., v_s].  alpha = beta = 0 is the monomial basis."""
+    s = len(alpha)
+    V = np.empty((u.shape[0], s))
+    prev, v = None, u
+    for i in range(s):
+        w = Ahat @ v - alpha[i] * v
+        if beta[i] != 0.0:
+            w = w + beta[i] * prev
+        V[:, i] = w
+        prev, v = v, w
+    return V
+
+
 def jacobi_scaled(A):
     """Return (Ahat = A D^{-1}, dinv) for the right Jacobi preconditioner M = D = diag(A)."""
     M = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
@@ -81,10 +148,15 @@ def _ls(H: np.ndarray, beta: float):
 def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None = None,
                 scheme: str = "one", intra: str = "rand", max_restarts: int = 200,
                 d: int | None = None, zeta: int = 8, seed: int = 42,
-                precond: str = "jacobi", preproc: str = "rand") -> GmresResult:
+                precond: str = "jacobi", preproc: str = "rand",
+                basis: str = "monomial") -> GmresResult:
     """s-step GMRES(m) with one-stage (RandCholQR or CholQR2 BCGS2) or two-stage
     (big panels of s_hat, preprocessed by RandBCGS2 or BCGS-PIP) block
-    orthogonalization."""
+    orthogonalization.  basis = "newton": the first cycle uses the monomial basis,
+    later cycles the Newton basis with shifts from the first cycle's Ritz values;
+    since Ahat U = W + U B for the generators U of a panel (B bidiagonal with
+    alpha on the diagonal and -beta above it), the Hessenberg matrix becomes
+    (Y + X B) X^{-1}."""
     if precond == "jacobi":
         Ahat, dinv = jacobi_scaled(A)
     else:
@@ -108,6 +180,18 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
         intra_fn = lambda W: rand_cholqr(W, sketch)  # noqa: E731
     else:
         intra_fn = cholqr2
+    alpha, beta_s = np.zeros(s), np.zeros(s)   # monomial until shifts are known
+
+    def gen(u):
+        return mpk_newton(Ahat, u, alpha, beta_s)
+
+    def shift_columns(Y, X, c0):
+        # Y(:, c0 + i) += alpha_i X(:, c0 + i) - beta_i X(:, c0 + i - 1)
+        for i in range(s):
+            Y[:m, c0 + i] += alpha[i] * X[:, c0 + i]
+            if beta_s[i] != 0.0:
+                Y[:m, c0 + i] -= beta_s[i] * X[:, c0 + i - 1]
+
     for cycle in range(max_restarts + 1):
         r = b - Ahat @ y
         try:
@@ -138,7 +222,7 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
             while ncols < m + 1:
                 P = ncols
                 if scheme == "one":
-                    V = mpk(Ahat, Qb[:, P - 1], s)
+                    V = gen(Qb[:, P - 1])
                     Qj, Rtop, Rjj = bcgs2_block(Qb[:, :P], V, intra_fn)
                     Qb[:, P:P + s] = Qj
                     R[:P, P:P + s] = Rtop
@@ -147,6 +231,7 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                     for i in range(1, s):
                         X[:P + i, P - 1 + i] = R[:P + i, P + i - 1]
                     Y[:P + s, P - 1:P - 1 + s] = R[:P + s, P:P + s]
+                    shift_columns(Y, X, P - 1)
                     ncols += s
                     its += s
                 else:
@@ -159,7 +244,7 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                         else:
                             u = bp.Qbar[:, -1]
                             gens.append(bp.cols - 1)
-                        bp.add_panel(mpk(Ahat, u, s))
+                        bp.add_panel(gen(u))
                     QB, RQB, RBB, cq = bp.finish()
                     Qb[:, P:P + s_hat] = QB
                     R[:P, P:P + s_hat] = RQB
@@ -173,6 +258,8 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                         for i in range(1, s):
                             X[:c + i, c - 1 + i] = R[:c + i, c + i - 1]
                     Y[:P + s_hat, P - 1:P - 1 + s_hat] = R[:P + s_hat, P:P + s_hat]
+                    for j in range(len(gens)):
+                        shift_columns(Y, X, P - 1 + j * s)
                     ncols += s_hat
                     its += s_hat
                 k = ncols - 1
@@ -188,6 +275,8 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
             return res
         k = ncols - 1
         y = y + Qb[:, :k] @ z
+        if basis == "newton" and cycle == 0:
+            alpha, beta_s = newton_shifts(H[:k, :k], s)
     res.iterations = its
     res.x = dinv * y
     return res

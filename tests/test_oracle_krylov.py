@@ -78,3 +78,86 @@ def test_x0_resume():
     g1 = krylov.sstep_gmres(A, b, s=5, m=20, tol=1e-4)
     g2 = krylov.sstep_gmres(A, b, g1.x, s=5, m=20, tol=1e-10)
     assert g2.converged and g2.history[0][1] <= 1e-4 * 1.0001
+
+
+# --- Newton basis (Bai, Hu and Reichel 1994) -----------------------------------------
+def test_newton_estimates_equal_householder_gmres():
+    # later cycles use the Newton basis of the first cycle's Ritz values; it spans the
+    # same Krylov space, so the residual estimates stay those of Householder GMRES
+    A = synth.laplace2d_csr(20)
+    b = synth.ones_rhs(A)
+    ref = dict(krylov.householder_gmres(A, b, m=20, tol=1e-11, max_restarts=3).estimates)
+    g = krylov.sstep_gmres(A, b, s=5, m=20, tol=1e-11, max_restarts=3, basis="newton")
+    checked = [(it, est) for it, est in g.estimates if it in ref and it > 20]
+    assert len(checked) >= 4
+    for it, est in checked:
+        assert abs(est - ref[it]) <= 1e-9 * ref[it]
+
+
+def test_leja_order_properties():
+    rng = np.random.default_rng(0)
+    re = rng.standard_normal(6)
+    cz = rng.standard_normal(3) + 1j * np.abs(rng.standard_normal(3))
+    theta = np.concatenate([re, cz, cz.conj()])
+    order = krylov.leja_order(theta)
+    assert len(order) == len(theta)
+    assert abs(order[0]) == max(abs(z) for z in theta)
+    for i, z in enumerate(order):                     # conjugates follow at once
+        if z.imag > 0:
+            assert order[i + 1] == z.conjugate()
+    # greedy criterion: each point (first of a pair) maximises the product of its
+    # distances to the points before it among the points still available
+    for i in range(1, len(order)):
+        if order[i].imag < 0:
+            continue
+        chosen, rest = order[:i], [z for z in order[i:] if z.imag >= 0]
+        prod = lambda z: np.prod([abs(z - w) for w in chosen])  # noqa: E731
+        assert prod(order[i]) >= max(prod(z) for z in rest) * (1 - 1e-12)
+
+
+def test_newton_shifts_special_cases():
+    # real spectrum: alpha = the eigenvalues in Leja order, beta = 0
+    H = np.diag([1.0, -3.0, 2.0, 0.5])
+    a, bt = krylov.newton_shifts(H, 4)
+    assert list(a) == [-3.0, 2.0, 0.5, 1.0] or list(a) == [-3.0, 2.0, 1.0, 0.5]
+    assert not bt.any()
+    # a rotation-like 2 x 2 block: eigenvalues 2 +- 3i -> (Re, Re) and (0, Im^2)
+    H = np.array([[2.0, -3.0], [3.0, 2.0]])
+    a, bt = krylov.newton_shifts(H, 2)
+    assert np.allclose(a, [2.0, 2.0]) and np.allclose(bt, [0.0, 9.0])
+    # the pair cut by the last position keeps only its real part
+    a, bt = krylov.newton_shifts(H, 1)
+    assert np.allclose(a, [2.0]) and not bt.any()
+    # zero shifts are the monomial basis
+    Ahat = synth.laplace2d_csr(8).to_scipy()
+    u = np.random.default_rng(1).standard_normal(Ahat.shape[0])
+    assert np.array_equal(krylov.mpk_newton(Ahat, u, np.zeros(4), np.zeros(4)), krylov.mpk(Ahat, u, 4))
+    # the recurrence v_{i+1} = (Ahat - alpha_i) v_i + beta_i v_{i-1} with a complex pair
+    # gives the real polynomial (Ahat - Re)^2 + Im^2 applied to u
+    V = krylov.mpk_newton(Ahat, u, np.array([0.7, 0.7]), np.array([0.0, 4.0]))
+    D = Ahat.toarray()
+    P = (D - 0.7 * np.eye(D.shape[0])) @ (D - 0.7 * np.eye(D.shape[0])) + 4.0 * np.eye(D.shape[0])
+    assert np.allclose(V[:, 1], P @ u, rtol=1e-12, atol=1e-10)
+
+
+def test_newton_basis_is_better_conditioned():
+    # the reason for the Newton basis: its panels are far better conditioned than the
+    # monomial ones at the same s
+    A = synth.poisson3d_csr(12)
+    Ahat, _ = krylov.jacobi_scaled(A)
+    u = np.random.default_rng(3).standard_normal(Ahat.shape[0])
+    u /= np.linalg.norm(u)
+    # Ritz values of a 40-step Arnoldi on Ahat
+    Q = np.zeros((Ahat.shape[0], 41))
+    Hh = np.zeros((41, 40))
+    Q[:, 0] = u
+    for j in range(40):
+        w = Ahat @ Q[:, j]
+        for i in range(j + 1):
+            Hh[i, j] = Q[:, i] @ w
+            w -= Hh[i, j] * Q[:, i]
+        Hh[j + 1, j] = np.linalg.norm(w)
+        Q[:, j + 1] = w / Hh[j + 1, j]
+    a, bt = krylov.newton_shifts(Hh[:40, :40], 10)
+    cond = lambda V: np.linalg.cond(V / np.linalg.norm(V, axis=0))  # noqa: E731
+    assert cond(krylov.mpk_newton(Ahat, u, a, bt)) < 1e-3 * cond(krylov.mpk(Ahat, u, 10))
