@@ -79,7 +79,8 @@ typedef struct rbo_opts {
   int32_t max_restarts;  /* GMRES: restart cycles allowed (default 1000 if <= 0)        */
   int32_t precond;       /* GMRES: 0 none, 1 Jacobi (M = diag(A), right preconditioner) */
   int32_t preproc;       /* two-stage: RBO_PREPROC_* (0 = RandBCGS2)                   */
-  int32_t reserved[2];
+  int32_t basis;         /* GMRES: RBO_BASIS_* (0 = monomial)                           */
+  int32_t reserved[1];
 } rbo_opts;
 
 #define RBO_STAGE_V0          1  /* normalisation of v_0                                  */
@@ -94,6 +95,12 @@ typedef struct rbo_opts {
 #define RBO_SKETCH_GAUSSIAN    1  /* dense N(0, 1) entries, generated from the seed        */
 #define RBO_SKETCH_COUNT_GAUSS 2  /* Count sketch to d_inner rows, then a d x d_inner
                                      Gaussian map                                        */
+
+/* matrix-powers basis of s-step GMRES (rbo_opts.basis) */
+#define RBO_BASIS_MONOMIAL    0  /* v_{i+1} = A M v_i (the paper's choice)                */
+#define RBO_BASIS_NEWTON      1  /* first cycle monomial, then Newton steps with the Leja-
+                                    ordered Ritz values of the first cycle's Hessenberg
+                                    matrix as shifts (rbo_newton_shifts)                 */
 
 /* two-stage preprocessing of the panels of a big panel (rbo_opts.preproc) */
 #define RBO_PREPROC_RAND      0  /* RandBCGS2: sketch + sketched BCGS2-HH (Section 7.2)  */
@@ -245,6 +252,18 @@ typedef struct rbo_csr {
  * Errors: RBO_ERR_ARG, RBO_ERR_CUDA.                                              */
 int rbo_mpk_csr(const rbo_csr* A, const double* dscale, int32_t s, const double* v0, double* V,
                 int64_t ldv, void* stream);
+
+/* Shifts of the Newton matrix-powers basis (Section 4 names it as the stabler option
+ * of Trilinos; Bai, Hu and Reichel 1994): the Ritz values (eigenvalues) of the k x k
+ * upper Hessenberg H (host, column-major, ld >= k; entries below the subdiagonal are
+ * ignored) in modified Leja order, as the real recurrence
+ *   v_{i+1} = (A - alpha_i) v_i + beta_i v_{i-1},  i = 0..s-1,
+ * alpha_i = Re theta_i, beta_i = (Im theta_i)^2 for the second value of a conjugate
+ * pair and 0 otherwise (a pair cut by the s-th position keeps its real part).
+ * alpha, beta: caller-owned host arrays of s doubles.  Host-only (no GPU needed).
+ * Errors: RBO_ERR_ARG, RBO_ERR_NOT_CONVERGED (QR iteration did not converge).      */
+int rbo_newton_shifts(const double* H, int64_t ld, int32_t k, int32_t s, double* alpha,
+                      double* beta);
 
 /* ---- s-step GMRES (Section 4, Figure 1) -------------------------------------------
  * (opts->preproc selects RandBCGS2 or BCGS-PIP for the two-stage panels)

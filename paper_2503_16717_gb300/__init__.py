@@ -49,6 +49,8 @@ INTRA_CHOLQR2 = 1
 STAGE_NAMES = {0: "", 1: "v0", 2: "intra", 3: "intra2", 4: "final", 5: "bigpanel", 6: "preproc"}
 PREPROC_RAND = 0
 PREPROC_PIP = 1
+BASIS_MONOMIAL = 0
+BASIS_NEWTON = 1
 SKETCH_SPARSE_SIGN = 0
 SKETCH_GAUSSIAN = 1
 SKETCH_COUNT_GAUSS = 2
@@ -57,7 +59,7 @@ SKETCH_COUNT_GAUSS = 2
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("v0", C.c_int32), ("intra", C.c_int32),
                 ("max_restarts", C.c_int32), ("precond", C.c_int32), ("preproc", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("basis", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class Info(C.Structure):
@@ -82,6 +84,7 @@ _vp, _i32, _i64, _u64, _dp = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_v
 SIGNATURES = {
     "rbo_sketch_create": (C.c_int, [_i64, _i32, _i32, _u64, C.POINTER(_vp)]),
     "rbo_sketch_create_ex": (C.c_int, [_i64, _i32, _i32, _i32, _i32, _u64, C.POINTER(_vp)]),
+    "rbo_newton_shifts": (C.c_int, [_dp, _i64, _i32, _i32, _dp, _dp]),
     "rbo_sketch_destroy": (C.c_int, [_vp]),
     "rbo_sketch_entries": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "rbo_sketch_apply": (C.c_int, [_vp, _i64, _i32, _vp, _i64, _dp, _i32, _vp]),
@@ -245,10 +248,10 @@ class OrthOut:
 
 
 def _opts(precision=PREC_FP64, v0=False, intra=INTRA_RANDCHOLQR, max_restarts=0, precond=1,
-          preproc=PREPROC_RAND) -> Opts:
+          preproc=PREPROC_RAND, basis=BASIS_MONOMIAL) -> Opts:
     o = Opts()
     o.precision, o.v0, o.intra, o.max_restarts, o.precond = precision, int(v0), intra, max_restarts, precond
-    o.preproc = preproc
+    o.preproc, o.basis = preproc, basis
     return o
 
 
@@ -326,7 +329,7 @@ def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int =
                 tol: float = 1e-10, sk: Sketch | None = None, precision: int = PREC_FP64,
                 precond: int = 1, max_restarts: int = 0, history_cap: int = 4096,
                 M=None, resid=None, intra: int = INTRA_RANDCHOLQR, preproc: int = PREPROC_RAND,
-                raise_on_error: bool = False):
+                basis: int = BASIS_MONOMIAL, raise_on_error: bool = False):
     """s-step GMRES(m); returns (x, info).  s_hat in (0, s] -> one-stage, else two-stage.
     ``M``: optional device tensor of preconditioner values on A's pattern (right
     preconditioner; overrides ``precond``)."""
@@ -341,7 +344,7 @@ def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int =
     if resid is not None:
         pr, nrr, cap, ldr = _mat(resid, "resid")
         info.resid, info.resid_ld, info.resid_cap = pr.value, ldr, cap
-    o = _opts(precision, False, intra, max_restarts, precond, preproc)
+    o = _opts(precision, False, intra, max_restarts, precond, preproc, basis)
     skh = sk.handle if sk is not None else None
     if M is not None:
         code = lib.rbo_sstep_gmres_precond(C.byref(st), _vec(M, "M"), _vec(b, "b"), _vec(x, "x"), s,
@@ -354,6 +357,16 @@ def sstep_gmres(A: DeviceCSR, b, x=None, *, s: int = 5, s_hat: int = 0, m: int =
     if code != OK and raise_on_error:
         raise RboError(code, "sstep_gmres", info)
     return x, d
+
+
+def newton_shifts(H, s: int):
+    """(alpha, beta) of the Newton basis from the square upper-Hessenberg H (host)."""
+    Hf = np.asfortranarray(np.asarray(H, dtype=np.float64))
+    k = Hf.shape[0]
+    a, b = np.zeros(s), np.zeros(s)
+    _check(lib.rbo_newton_shifts(Hf.ctypes.data_as(C.c_void_p), k, k, s, a.ctypes.data_as(C.c_void_p),
+                                 b.ctypes.data_as(C.c_void_p)), "newton_shifts")
+    return a, b
 
 
 # ---- learned SPAI preconditioner -----------------------------------------------------------

@@ -161,6 +161,28 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   bool converged = false;
   double relres = INFINITY, est_rel = INFINITY;
   int cycle = 0, fallbacks = 0;
+  // Newton basis: shifts from the first cycle's Ritz values (monomial until then).
+  // The generators U of a panel satisfy A M U = W + U B with B bidiagonal (alpha on
+  // the diagonal, -beta above it), so the Hessenberg matrix is (Y + X B) X^{-1}.
+  const bool newton = opts && opts->basis == RBO_BASIS_NEWTON;
+  std::vector<double> sh_a(s, 0.0), sh_b(s, 0.0);
+  bool shifted = false;
+  // output i of a panel from generators g_i (and g_{i-1})
+  auto gen_step = [&](const double* gi, const double* gprev, double* out, int i) -> int {
+    int r = apply_op(gi, out);
+    if (r || !shifted) return r;
+    return shift_launch(n, out, gi, -sh_a[i], gprev, sh_b[i], st);
+  };
+  // Y(:, c0 + i) += alpha_i X(:, c0 + i) - beta_i X(:, c0 + i - 1)
+  auto shift_columns = [&](int c0) {
+    if (!shifted) return;
+    for (int i = 0; i < s; ++i)
+      for (int r = 0; r < m; ++r) {
+        double v = sh_a[i] * X[r + (size_t)(c0 + i) * m];
+        if (sh_b[i] != 0.0) v -= sh_b[i] * X[r + (size_t)(c0 + i - 1) * m];
+        Y[r + (size_t)(c0 + i) * ld] += v;
+      }
+  };
   // Mixed precision: a block that the float32 sketch could not precondition (loss of
   // orthogonality or a Cholesky breakdown) makes the restart cycle start over in
   // float64, which stays on for the rest of the solve; x is only updated at the end of
@@ -224,7 +246,10 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
         double* W = w.Qb + (int64_t)P * ldq;
         const double* u = w.Qb + (int64_t)(P - 1) * ldq;
         for (int i = 0; i < s; ++i)
-          if ((e = apply_op(i == 0 ? u : W + (int64_t)(i - 1) * ldq, W + (int64_t)i * ldq))) return e;
+          if ((e = gen_step(i == 0 ? u : W + (int64_t)(i - 1) * ldq,
+                            i == 0 ? nullptr : (i == 1 ? u : W + (int64_t)(i - 2) * ldq),
+                            W + (int64_t)i * ldq, i)))
+            return e;
         if ((e = one_stage_block(c, n, w.Qb, ldq, P, W, ldq, s, intra, w.Rdev, ld, P, blk)))
           return e;
         if (cudaMemcpy2DAsync(Rh.data() + (size_t)P * ld, (size_t)ld * 8, w.Rdev + (size_t)P * ld,
@@ -243,6 +268,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
           for (int r = 0; r < P + i; ++r) X[r + (size_t)(P - 1 + i) * m] = Rh[r + (size_t)(P + i - 1) * ld];
         for (int i = 0; i < s; ++i)
           for (int r = 0; r < P + s; ++r) Y[r + (size_t)(P - 1 + i) * ld] = Rh[r + (size_t)(P + i) * ld];
+        shift_columns(P - 1);
         ncols += s;
         its += s;
       } else {
@@ -261,7 +287,9 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
           }
           double* W = bp.VB + (int64_t)bp.cols * ldq;
           for (int i = 0; i < s; ++i)
-            if ((e = apply_op(i == 0 ? u : W + (int64_t)(i - 1) * ldq, W + (int64_t)i * ldq)))
+            if ((e = gen_step(i == 0 ? u : W + (int64_t)(i - 1) * ldq,
+                              i == 0 ? nullptr : (i == 1 ? u : W + (int64_t)(i - 2) * ldq),
+                              W + (int64_t)i * ldq, i)))
               return e;
           if ((e = bigpanel_add(c, bp, s))) return e;
         }
@@ -294,6 +322,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
         }
         for (int i = 0; i < K; ++i)
           for (int r = 0; r < P + K; ++r) Y[r + (size_t)(P - 1 + i) * ld] = Rh[r + (size_t)(P + i) * ld];
+        for (int j = 0; j < (int)gens.size(); ++j) shift_columns(P - 1 + j * s);
         ncols += K;
         its += K;
       }
@@ -333,6 +362,10 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
     } else {
       if ((e = axpy_scaled_launch(n, w.dscale, w.t1, x, st))) return e;
       c.launches += 2;
+    }
+    if (newton && !shifted && k >= 1) {
+      // Ritz values of the first cycle (kept monomial when the QR iteration fails)
+      if (newton_shifts(H.data(), ld, k, s, sh_a.data(), sh_b.data()) == RBO_OK) shifted = true;
     }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return RBO_ERR_CUDA;
@@ -389,6 +422,8 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   if (code == RBO_OK && !pip && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 &&
       opts->precision != RBO_PREC_MIXED && opts->precision != RBO_PREC_DF64)
+    code = RBO_ERR_ARG;
+  if (code == RBO_OK && opts && opts->basis != RBO_BASIS_MONOMIAL && opts->basis != RBO_BASIS_NEWTON)
     code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->intra != RBO_INTRA_RANDCHOLQR &&
       (opts->intra != RBO_INTRA_CHOLQR2 || s_hat > s))

@@ -211,6 +211,9 @@ int gemv_update_launch(int64_t n, int k, const double* Q, int64_t ldq, const dou
                        int accumulate, cudaStream_t st);
 // x += diag(ds) t  (ds null: x += t)
 int axpy_scaled_launch(int64_t n, const double* ds, const double* t, double* x, cudaStream_t st);
+// out += a u + b uprev (the Newton-basis step; uprev unused when b == 0)
+int shift_launch(int64_t n, double* out, const double* u, double a, const double* uprev, double b,
+                 cudaStream_t st);
 // mode 0: x = dscale .* y;  mode 1: x = y ./ dscale  (dscale null: copy)
 int scale_vec_launch(int64_t n, const double* dscale, const double* y, double* x, int mode,
                      cudaStream_t st);
@@ -240,6 +243,8 @@ int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax, int64_t n);
 // Arena bytes orth_ctx_alloc will need.
 // (d: rows of the final sketch; type RBO_SKETCH_*; d_inner: Count-Gauss Count stage)
 size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta, int type, int d_inner);
+// Newton-basis shifts from the k x k upper Hessenberg H (ld ld): alpha, beta (s each).
+int newton_shifts(const double* H, int64_t ld, int k, int s, double* alpha, double* beta);
 // Sketch fields of a row pass that applies the call's sketch.
 void set_sketch(RowPass& r, const OrthCtx& c);
 // Largest reduced-vector length of any pass for these sizes.

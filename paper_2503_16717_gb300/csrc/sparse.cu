@@ -257,6 +257,24 @@ int axpy_scaled_launch(int64_t n, const double* ds, const double* t, double* x, 
   return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
 }
 
+// Newton-basis step: out += a u + b uprev (uprev may be null when b = 0)
+__global__ void shift_kernel(int64_t n, double* __restrict__ out, const double* __restrict__ u,
+                             double a, const double* __restrict__ uprev, double b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = fma(a, u[i], out[i]);
+  if (uprev) v = fma(b, uprev[i], v);
+  out[i] = v;
+}
+
+int shift_launch(int64_t n, double* out, const double* u, double a, const double* uprev, double b,
+                 cudaStream_t st) {
+  if (n <= 0) return RBO_OK;
+  shift_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, out, u, a, b != 0.0 ? uprev : nullptr,
+                                                              b);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
 int gemv_update_launch(int64_t n, int k, const double* Q, int64_t ldq, const double* z, double* y,
                        int accumulate, cudaStream_t st) {
   if (n <= 0 || k <= 0) return RBO_OK;

@@ -220,3 +220,34 @@ def test_gmres_with_gaussian_sketches(rbo, kind):
         assert info["converged"] == 1
         assert abs(info["iterations"] - ref["iterations"]) <= s_hat
         assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6
+
+
+@pytest.mark.parametrize("N,s,s_hat,m", [(16, 5, 0, 30), (16, 10, 0, 60), (16, 5, 10, 30)])
+def test_newton_basis_gmres_matches_oracle(rbo, N, s, s_hat, m):
+    import torch
+    A = synth.poisson3d_csr(N)
+    b = synth.ones_rhs(A)
+    x, info = rbo.sstep_gmres(rbo.DeviceCSR.from_host(A), torch.from_numpy(b).cuda(), s=s,
+                              s_hat=s_hat, m=m, tol=1e-10, basis=rbo.BASIS_NEWTON)
+    scheme = "two" if s_hat > s else "one"
+    ref = krylov.sstep_gmres(A, b, s=s, m=m, s_hat=(s_hat or None), scheme=scheme, tol=1e-10,
+                             basis="newton")
+    assert info["status"] == 0 and info["converged"] == 1 and ref.converged
+    gran = s_hat if s_hat > s else s
+    assert abs(info["iterations"] - ref.iterations) <= gran
+    assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6
+
+
+def test_newton_basis_nonsymmetric(rbo):
+    # complex Ritz values: conjugate pairs in the real recurrence
+    import torch
+    A, _ = synth.convdiff2d_csr(48, seed=1002)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    bd = torch.from_numpy(b).cuda()
+    x, info = rbo.sstep_gmres(Ad, bd, s=10, m=60, tol=1e-10, basis=rbo.BASIS_NEWTON)
+    ref = krylov.sstep_gmres(A, b, s=10, m=60, tol=1e-10, basis="newton")
+    assert info["converged"] == 1 and ref.converged
+    assert abs(info["iterations"] - ref.iterations) <= 10
+    r = b - A.to_scipy() @ x.cpu().numpy()
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
