@@ -152,8 +152,9 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                 basis: str = "monomial") -> GmresResult:
     """s-step GMRES(m) with one-stage (RandCholQR or CholQR2 BCGS2) or two-stage
     (big panels of s_hat, preprocessed by RandBCGS2 or BCGS-PIP) block
-    orthogonalization.  basis = "newton": the first cycle uses the monomial basis,
-    later cycles the Newton basis with shifts from the first cycle's Ritz values;
+    orthogonalization.  basis = "newton": the first cycle is standard GMRES (panels
+    of one column), later cycles use the Newton basis with shifts from the first
+    cycle's Ritz values;
     since Ahat U = W + U B for the generators U of a panel (B bidiagonal with
     alpha on the diagonal and -beta above it), the Hessenberg matrix becomes
     (Y + X B) X^{-1}."""
@@ -182,12 +183,12 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
         intra_fn = cholqr2
     alpha, beta_s = np.zeros(s), np.zeros(s)   # monomial until shifts are known
 
-    def gen(u):
-        return mpk_newton(Ahat, u, alpha, beta_s)
+    def gen(u, k):
+        return mpk_newton(Ahat, u, alpha[:k], beta_s[:k])
 
-    def shift_columns(Y, X, c0):
+    def shift_columns(Y, X, c0, k):
         # Y(:, c0 + i) += alpha_i X(:, c0 + i) - beta_i X(:, c0 + i - 1)
-        for i in range(s):
+        for i in range(k):
             Y[:m, c0 + i] += alpha[i] * X[:, c0 + i]
             if beta_s[i] != 0.0:
                 Y[:m, c0 + i] -= beta_s[i] * X[:, c0 + i - 1]
@@ -218,22 +219,25 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
         Y = np.zeros((m + 1, m))
         ncols = 1
         z = np.zeros(0)
+        # Newton basis: the cycle that provides the Ritz values is standard GMRES
+        # (panels of one column, one-stage)
+        sc = 1 if (basis == "newton" and cycle == 0) else s
         try:
             while ncols < m + 1:
                 P = ncols
-                if scheme == "one":
-                    V = gen(Qb[:, P - 1])
+                if scheme == "one" or sc != s:
+                    V = gen(Qb[:, P - 1], sc)
                     Qj, Rtop, Rjj = bcgs2_block(Qb[:, :P], V, intra_fn)
-                    Qb[:, P:P + s] = Qj
-                    R[:P, P:P + s] = Rtop
-                    R[P:P + s, P:P + s] = Rjj
+                    Qb[:, P:P + sc] = Qj
+                    R[:P, P:P + sc] = Rtop
+                    R[P:P + sc, P:P + sc] = Rjj
                     X[P - 1, P - 1] = 1.0
-                    for i in range(1, s):
+                    for i in range(1, sc):
                         X[:P + i, P - 1 + i] = R[:P + i, P + i - 1]
-                    Y[:P + s, P - 1:P - 1 + s] = R[:P + s, P:P + s]
-                    shift_columns(Y, X, P - 1)
-                    ncols += s
-                    its += s
+                    Y[:P + sc, P - 1:P - 1 + sc] = R[:P + sc, P:P + sc]
+                    shift_columns(Y, X, P - 1, sc)
+                    ncols += sc
+                    its += sc
                 else:
                     bp = TwoStageBigPanel(Qb[:, :P], sketch, s_hat, preproc)
                     gens = []
@@ -244,7 +248,7 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                         else:
                             u = bp.Qbar[:, -1]
                             gens.append(bp.cols - 1)
-                        bp.add_panel(gen(u))
+                        bp.add_panel(gen(u, s))
                     QB, RQB, RBB, cq = bp.finish()
                     Qb[:, P:P + s_hat] = QB
                     R[:P, P:P + s_hat] = RQB
@@ -259,7 +263,7 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                             X[:c + i, c - 1 + i] = R[:c + i, c + i - 1]
                     Y[:P + s_hat, P - 1:P - 1 + s_hat] = R[:P + s_hat, P:P + s_hat]
                     for j in range(len(gens)):
-                        shift_columns(Y, X, P - 1 + j * s)
+                        shift_columns(Y, X, P - 1 + j * s, s)
                     ncols += s_hat
                     its += s_hat
                 k = ncols - 1

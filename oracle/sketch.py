@@ -119,7 +119,8 @@ class Sketch:
 # definitions, independently of the CUDA library):
 #   stream seed  seed_g = seed XOR GAUSS_SALT
 #   entry (k, r) of a Gaussian map with d rows uses output i = r * d + k + 1;
-#   u1 = (top 24 bits of h + 1/2) / 2^24 in (0, 1), u2 = (bits 16..39 of h) / 2^24;
+#   m1 = top 24 bits of h, u1 = float32(m1 + 1/2) / 2^24 in (0, 1) (the sum rounded to
+#   float32), u2 = (bits 16..39 of h) / 2^24;
 #   theta = sqrt(-2 ln u1) cos(2 pi u2) (Box and Muller 1958), rounded to float32
 #   (the CUDA side evaluates it in float32 arithmetic, within a few float32 ulps).
 GAUSS_SALT = 0x2545F4914F6CDD1D
@@ -133,7 +134,7 @@ def gaussian_entries(seed: int, rows: np.ndarray, d: int) -> np.ndarray:
     with np.errstate(over="ignore"):
         i = rows[:, None] * np.uint64(d) + k[None, :] + np.uint64(1)
     h = splitmix64_output(int(np.uint64(seed) ^ np.uint64(GAUSS_SALT)), i)
-    u1 = ((h >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24
+    u1 = ((h >> np.uint64(40)).astype(np.float64) + 0.5).astype(np.float32).astype(np.float64) * 2.0 ** -24
     u2 = ((h >> np.uint64(16)) & np.uint64(0xFFFFFF)).astype(np.float64) * 2.0 ** -24
     g = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
     return g.astype(np.float32).astype(np.float64)

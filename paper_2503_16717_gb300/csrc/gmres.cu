@@ -240,20 +240,24 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
     int ncols = 1;
     int blk = 0;
     bool redo = false;
+    // Newton basis: the cycle that provides the Ritz values runs standard GMRES
+    // (panels of one column, one-stage), which does not depend on the conditioning
+    // of a monomial panel; later cycles use panels of s Newton vectors
+    const int sc = (newton && !shifted) ? 1 : s;
     while (ncols < m + 1) {
       const int P = ncols;
-      if (!two) {
+      if (!two || sc != s) {
         double* W = w.Qb + (int64_t)P * ldq;
         const double* u = w.Qb + (int64_t)(P - 1) * ldq;
-        for (int i = 0; i < s; ++i)
+        for (int i = 0; i < sc; ++i)
           if ((e = gen_step(i == 0 ? u : W + (int64_t)(i - 1) * ldq,
                             i == 0 ? nullptr : (i == 1 ? u : W + (int64_t)(i - 2) * ldq),
                             W + (int64_t)i * ldq, i)))
             return e;
-        if ((e = one_stage_block(c, n, w.Qb, ldq, P, W, ldq, s, intra, w.Rdev, ld, P, blk)))
+        if ((e = one_stage_block(c, n, w.Qb, ldq, P, W, ldq, sc, intra, w.Rdev, ld, P, blk)))
           return e;
         if (cudaMemcpy2DAsync(Rh.data() + (size_t)P * ld, (size_t)ld * 8, w.Rdev + (size_t)P * ld,
-                              (size_t)ld * 8, (size_t)(P + s) * 8, s, cudaMemcpyDeviceToHost,
+                              (size_t)ld * 8, (size_t)(P + sc) * 8, sc, cudaMemcpyDeviceToHost,
                               st) != cudaSuccess)
           return RBO_ERR_CUDA;
         if ((e = finish_status(ar, st, info))) {
@@ -264,13 +268,13 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
           return e;
         }
         X[(P - 1) + (size_t)(P - 1) * m] = 1.0;
-        for (int i = 1; i < s; ++i)
+        for (int i = 1; i < sc; ++i)
           for (int r = 0; r < P + i; ++r) X[r + (size_t)(P - 1 + i) * m] = Rh[r + (size_t)(P + i - 1) * ld];
-        for (int i = 0; i < s; ++i)
-          for (int r = 0; r < P + s; ++r) Y[r + (size_t)(P - 1 + i) * ld] = Rh[r + (size_t)(P + i) * ld];
+        for (int i = 0; i < sc; ++i)
+          for (int r = 0; r < P + sc; ++r) Y[r + (size_t)(P - 1 + i) * ld] = Rh[r + (size_t)(P + i) * ld];
         shift_columns(P - 1);
-        ncols += s;
-        its += s;
+        ncols += sc;
+        its += sc;
       } else {
         BigPanel bp;
         bp.n = n; bp.Q = w.Qb; bp.ldq = ldq; bp.P = P;
