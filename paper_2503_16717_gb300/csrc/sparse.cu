@@ -48,12 +48,14 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, int64_t nnz,
 }
 
 
-// Short rows: each warp takes 32 consecutive rows.  The warp stages the entries of its
-// rows in chunks of SCH (coalesced index and value loads, the x gathers issued by the
-// same lanes), then every lane runs the multiply-adds of its own row from shared
-// memory, as two interleaved chains (even and odd entries) added at the end.  No
-// cross-lane float64 reduction is needed: each float64 operation costs a slot of this
-// GPU's narrow float64 pipe.
+// Short rows: each warp takes groups of 32 consecutive rows (persistent grid of 4
+// blocks per SM; the row pointers of the warp's next group are loaded while the
+// current group is processed).  The warp stages the entries of its rows in chunks of
+// SCH (coalesced index and value loads, the x gathers issued by the same lanes), then
+// every lane runs the multiply-adds of its own row from shared memory, as two
+// interleaved chains (even and odd entries) added at the end.  No cross-lane float64
+// reduction is needed: each float64 operation costs a slot of this GPU's narrow
+// float64 pipe.
 constexpr int SCH = 256;
 __global__ void __launch_bounds__(256) spmv_stream_kernel(int64_t n, int64_t nnz,
                                                           const int32_t* __restrict__ rowptr,
@@ -65,76 +67,84 @@ __global__ void __launch_bounds__(256) spmv_stream_kernel(int64_t n, int64_t nnz
                                                           double* __restrict__ y, DevStatus* status) {
   __shared__ double sv[8][SCH], sx[8][SCH];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t r0 = ((int64_t)blockIdx.x * 8 + warp) * 32;
-  if (r0 >= n) return;
-  const int64_t r = r0 + lane;
-  const int nr = (int)((n - r0) < 32 ? (n - r0) : 32);
+  const int64_t ngroups = (n + 31) / 32;
+  const int64_t gstride = (int64_t)gridDim.x * 8;
+  int64_t g = (int64_t)blockIdx.x * 8 + warp;
   int beg = 0, end = 0;
-  if (r < n) {
-    beg = __ldg(rowptr + r);
-    end = __ldg(rowptr + r + 1);
+  if (g < ngroups && g * 32 + lane < n) {
+    beg = __ldg(rowptr + g * 32 + lane);
+    end = __ldg(rowptr + g * 32 + lane + 1);
   }
-  // the warp's entry range, from its first and last row
-  const int e0 = __shfl_sync(0xffffffffu, beg, 0);
-  const int e1 = __shfl_sync(0xffffffffu, end, nr - 1);
-  const bool range_ok = e0 >= 0 && e1 >= e0 && (int64_t)e1 <= nnz;
-  if (r < n && (!range_ok || beg < e0 || end < beg || end > e1)) {
-    if (status) set_error(status, RBO_ERR_ARG, 11);
-    end = beg;
-  }
-  double s = 0.0, s2 = 0.0;
-  if (range_ok) {
-    for (int c0 = e0; c0 < e1; c0 += SCH) {
-      const int cn = (e1 - c0) < SCH ? (e1 - c0) : SCH;
-      // all index and value loads first, then all gathers, then the stores: every
-      // load of a chunk is in flight at once
-      int cj[SCH / 32];
-      double v[SCH / 32], xv[SCH / 32];
+  for (; g < ngroups; g += gstride) {
+    // row pointers of this warp's next group, in flight during this group
+    const int64_t gn = g + gstride;
+    int nbeg = 0, nend = 0;
+    if (gn < ngroups && gn * 32 + lane < n) {
+      nbeg = __ldg(rowptr + gn * 32 + lane);
+      nend = __ldg(rowptr + gn * 32 + lane + 1);
+    }
+    const int64_t r0 = g * 32, r = r0 + lane;
+    const int nr = (int)((n - r0) < 32 ? (n - r0) : 32);
+    const int e0 = __shfl_sync(0xffffffffu, beg, 0);
+    const int e1 = __shfl_sync(0xffffffffu, end, nr - 1);
+    const bool range_ok = e0 >= 0 && e1 >= e0 && (int64_t)e1 <= nnz;
+    if (r < n && (!range_ok || beg < e0 || end < beg || end > e1)) {
+      if (status) set_error(status, RBO_ERR_ARG, 11);
+      end = beg;
+    }
+    double s = 0.0, s2 = 0.0;
+    if (range_ok) {
+      for (int c0 = e0; c0 < e1; c0 += SCH) {
+        const int cn = (e1 - c0) < SCH ? (e1 - c0) : SCH;
+        int cj[SCH / 32];
+        double v[SCH / 32], xv[SCH / 32];
 #pragma unroll
-      for (int u = 0; u < SCH / 32; ++u) {
-        const int t = u * 32 + lane;
-        cj[u] = -1;
-        v[u] = 0.0;
-        if (t < cn) {
-          cj[u] = __ldg(col + c0 + t);
-          v[u] = __ldg(val + c0 + t);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < SCH / 32; ++u) {
-        const int t = u * 32 + lane;
-        xv[u] = 0.0;
-        if (t < cn) {
-          if (cj[u] < 0 || (int64_t)cj[u] >= n) {
-            if (status) set_error(status, RBO_ERR_ARG, 12);
-            v[u] = 0.0;
-          } else {
-            xv[u] = dscale ? __ldg(dscale + cj[u]) * __ldg(x + cj[u]) : __ldg(x + cj[u]);
+        for (int u = 0; u < SCH / 32; ++u) {
+          const int t = u * 32 + lane;
+          cj[u] = -1;
+          v[u] = 0.0;
+          if (t < cn) {
+            cj[u] = __ldg(col + c0 + t);
+            v[u] = __ldg(val + c0 + t);
           }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < SCH / 32; ++u) {
-        const int t = u * 32 + lane;
-        if (t < cn) {
-          sv[warp][t] = v[u];
-          sx[warp][t] = xv[u];
+        for (int u = 0; u < SCH / 32; ++u) {
+          const int t = u * 32 + lane;
+          xv[u] = 0.0;
+          if (t < cn) {
+            if (cj[u] < 0 || (int64_t)cj[u] >= n) {
+              if (status) set_error(status, RBO_ERR_ARG, 12);
+              v[u] = 0.0;
+            } else {
+              xv[u] = dscale ? __ldg(dscale + cj[u]) * __ldg(x + cj[u]) : __ldg(x + cj[u]);
+            }
+          }
         }
+#pragma unroll
+        for (int u = 0; u < SCH / 32; ++u) {
+          const int t = u * 32 + lane;
+          if (t < cn) {
+            sv[warp][t] = v[u];
+            sx[warp][t] = xv[u];
+          }
+        }
+        __syncwarp();
+        const int lo = beg > c0 ? beg : c0, hi = end < c0 + cn ? end : c0 + cn;
+        int e = lo;
+        for (; e + 1 < hi; e += 2) {
+          s = fma(sv[warp][e - c0], sx[warp][e - c0], s);
+          s2 = fma(sv[warp][e + 1 - c0], sx[warp][e + 1 - c0], s2);
+        }
+        if (e < hi) s = fma(sv[warp][e - c0], sx[warp][e - c0], s);
+        __syncwarp();
       }
-      __syncwarp();
-      const int lo = beg > c0 ? beg : c0, hi = end < c0 + cn ? end : c0 + cn;
-      // two interleaved chains (entries of even and odd position in the row)
-      int e = lo;
-      for (; e + 1 < hi; e += 2) {
-        s = fma(sv[warp][e - c0], sx[warp][e - c0], s);
-        s2 = fma(sv[warp][e + 1 - c0], sx[warp][e + 1 - c0], s2);
-      }
-      if (e < hi) s = fma(sv[warp][e - c0], sx[warp][e - c0], s);
-      __syncwarp();
     }
+    s += s2;
+    if (r < n) y[r] = bvec ? (bvec[r] - s) : s;
+    beg = nbeg;
+    end = nend;
   }
-  s += s2;
-  if (r < n) y[r] = bvec ? (bvec[r] - s) : s;
 }
 
 static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
@@ -166,7 +176,10 @@ static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const doub
                                const double* b, double* y, DevStatus* status, cudaStream_t st) {
   const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
   if (avg <= 12.0) {
-    const int64_t blocks = (A.n + 255) / 256;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t blocks = std::min<int64_t>((A.n + 255) / 256, (int64_t)std::max(sms, 1) * 4);
     spmv_stream_kernel<<<(unsigned)blocks, 256, 0, st>>>(A.n, A.nnz, A.rowptr, A.col, A.val, dscale,
                                                           x, b, y, status);
   } else if (avg <= 24.0)
