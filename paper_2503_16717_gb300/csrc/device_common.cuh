@@ -79,6 +79,51 @@ __device__ __forceinline__ float gauss_entry(uint64_t seed, uint64_t r, int k, i
   return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
+// ---- fixed-point tile sums (integer ALU) ----------------------------------------------
+// A column of a tile with largest exponent field E is summed exactly in int64 fixed
+// point with unit 2^(E - 1023 - 54): every finite value converts with |v| < 2^55
+// (round half away from zero below the unit; zero and subnormal values give 0), so
+// sums of up to 128 values stay below 2^62.
+__device__ __forceinline__ long long fix_from_double(double y, int E) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(y);
+  const int e = (int)((u >> 52) & 0x7FF);
+  if (e == 0) return 0;
+  const unsigned long long M = (u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const int sh = e - E + 2;  // <= 2
+  unsigned long long v;
+  if (sh >= 0) {
+    v = M << sh;
+  } else if (sh > -64) {
+    const int k = -sh;
+    v = (M + (1ULL << (k - 1))) >> k;
+  } else {
+    v = 0;
+  }
+  return (u >> 63) ? -(long long)v : (long long)v;
+}
+// s * 2^(E - 1023 - 54) rounded to a float64 (ties away from zero), integer ALU only
+__device__ __forceinline__ double double_from_fix(long long s, int E) {
+  if (s == 0) return 0.0;
+  const unsigned long long neg = s < 0 ? 1ULL : 0ULL;
+  const unsigned long long a = neg ? (unsigned long long)(-s) : (unsigned long long)s;
+  const int nb = 64 - __clzll((long long)a);
+  int ef = nb + E - 55;
+  unsigned long long m;
+  if (nb > 53) {
+    const int k = nb - 53;
+    m = (a + (1ULL << (k - 1))) >> k;
+    if (m >> 53) {
+      m >>= 1;
+      ++ef;
+    }
+  } else {
+    m = a << (53 - nb);
+  }
+  if (ef <= 0) return 0.0;
+  if (ef >= 0x7FF) return __longlong_as_double((long long)((neg << 63) | 0x7FF0000000000000ULL));
+  return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)ef << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+}
+
 // ---- float64 -> float32 by integer operations ----------------------------------------
 // The f64->f32 conversion instruction runs on the float64 pipe of this GPU; this
 // version uses integer ALU only: round to nearest on the 29 dropped mantissa bits

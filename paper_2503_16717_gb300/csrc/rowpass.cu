@@ -365,25 +365,35 @@ __device__ __forceinline__ void gram_rows_df(df (&acc)[CB], const df* z, const d
     for (int c = 0; c < CW; ++c) df_fma_acc(acc[c], zv, y[(size_t)c * TP + rr]);
   }
 }
-// Sketch of one sketch row over a tile: acc[c * d] += sum_t sign_t y[c][row_t] for CW
-// columns, entries in list order.  The sign is applied by flipping the sign bit: a
-// float64 negation would take a second slot of the (scarce) float64 pipe.
+// Sketch of one sketch row over a tile, float64 path: the tile's values of each column
+// are held as int64 fixed point (unit 2^(E_c - 1077), E_c the column's largest
+// exponent field in the tile; fix_from_double); the row's entries are summed exactly
+// in integers (signs by integer negation), and the exact tile sum is rounded once to
+// float64 and added to the accumulator: one float64 add per (sketch row, column) and
+// tile instead of one per entry, on every lane.  A column with a non-finite value in
+// the tile (E_c = 0x7FF) makes the accumulators NaN.
 template <int CW>
-__device__ __forceinline__ void sketch_row_f64(double* acc, int d, const double* y, int TP,
-                                               const uint8_t* e, int cnt) {
-  double v[CW];
+__device__ __forceinline__ void sketch_row_fix(double* acc, int d, const long long* y, int TP,
+                                               const int* emax, const uint8_t* e, int cnt) {
+  long long v[CW];
 #pragma unroll
-  for (int c = 0; c < CW; ++c) v[c] = acc[(size_t)c * d];
+  for (int c = 0; c < CW; ++c) v[c] = 0;
   for (int t = 0; t < cnt; ++t) {
     const int ev = e[t];
     const int r = ev >> 1;
-    const long long sg = (long long)(ev & 1) << 63;
+    const long long ng = -(long long)(ev & 1);  // 0 or all ones
 #pragma unroll
-    for (int c = 0; c < CW; ++c)
-      v[c] += __longlong_as_double(__double_as_longlong(y[(size_t)c * TP + r]) ^ sg);
+    for (int c = 0; c < CW; ++c) {
+      const long long f = y[(size_t)c * TP + r];
+      v[c] += (f ^ ng) - ng;                     // f or -f
+    }
   }
 #pragma unroll
-  for (int c = 0; c < CW; ++c) acc[(size_t)c * d] = v[c];
+  for (int c = 0; c < CW; ++c) {
+    const double add = emax[c] == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
+                                        : double_from_fix(v[c], emax[c]);
+    acc[(size_t)c * d] += add;
+  }
 }
 // float32 values in the first 4 bytes of each 8-byte slot: y holds 2 floats per row
 template <int CW>
@@ -417,16 +427,19 @@ __device__ __forceinline__ void sketch_row_f32(float* acc, int d, const float* y
 // ------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------
-template <int ARITH>
+template <int ARITH, bool SK>
 __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const __grid_constant__ PassDev P) {
   // ARITH 0: float64; 1: float32 for X^T Y' and the sketch (mixed precision);
-  // 2: float32 pairs for the transform and the Gram, float64 for the sketch
+  // 2: float32 pairs for the transform and the Gram, float64 for the sketch.
+  // SK: the pass scatters a sparse sketch (and has no Gram); separate instances keep
+  // each loop's registers to itself.
   constexpr bool MIXED = ARITH == 1;
   constexpr bool DF = ARITH == 2;
   constexpr int IPTA = DF ? 2 : IPT;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_flag;
   __shared__ int s_last;
+  __shared__ int s_emax[64];  // sketch: largest exponent field per column of the tile
   const RowPass& rp = P.p;
   if (read_code(P.status) != 0) return;
 
@@ -444,7 +457,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
   double* gth = reinterpret_cast<double*>(smem + P.off_gth);  // Gaussian sketch tile
   float* skf = reinterpret_cast<float*>(smem + P.off_sk);
   const int d = rp.sk_d;
-  const bool do_sk = d > 0;
+  const bool do_sk = SK && d > 0;
 
   // small matrices + sketch copies
   if (rp.C) {
@@ -699,7 +712,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
       }
       __syncthreads();
     }
-    if (DF && P.no > 0) {
+    if (!SK && DF && P.no > 0) {
 #pragma unroll
       for (int k = 0; k < IPTA; ++k) {
         const int task = tid + k * NT;
@@ -719,7 +732,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
         flush();
         since_flush = 0;
       }
-    } else if (P.no > 0) {
+    } else if (!SK && P.no > 0) {
 #pragma unroll
       for (int k = 0; k < IPTA; ++k) {
         const int task = tid + k * NT;
@@ -749,6 +762,27 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
     // and the count-sorted slots keep the lanes of a warp on equal trip counts.
     if (do_sk) {
       __syncthreads();  // y' of this tile complete
+      if (!MIXED) {
+        // per column: the largest exponent field of the tile, then the values in
+        // place as int64 fixed point (y' is not read again in a sketch pass)
+        for (int c = tid; c < b; c += NT) s_emax[c] = 0;
+        __syncthreads();
+        for (int t = tid; t < b * T; t += NT) {
+          const int c = t / T, r = t % T;
+          const unsigned long long u = (unsigned long long)__double_as_longlong(ys[(size_t)c * TP + r]);
+          const int ex = (int)((u >> 52) & 0x7FF);
+          if (r < rows && ex != 0) atomicMax(&s_emax[c], ex);
+        }
+        __syncthreads();
+        for (int t = tid; t < b * T; t += NT) {
+          const int c = t / T, r = t % T;
+          const int E = s_emax[c];
+          const double yv = ys[(size_t)c * TP + r];
+          reinterpret_cast<long long*>(ys)[(size_t)c * TP + r] =
+              (r < rows && E != 0x7FF) ? fix_from_double(yv, E) : 0LL;
+        }
+        __syncthreads();
+      }
       const uint32_t* meta = reinterpret_cast<const uint32_t*>(stage_R(s));
       const uint8_t* lst = reinterpret_cast<const uint8_t*>(meta + rp.sk.mcap);
       for (int q = tid; q < rp.sk.mcap; q += NT) {
@@ -763,10 +797,10 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const
                             reinterpret_cast<const float*>(ys + (size_t)c0 * TP), 2 * TP, e, cnt)
           }
         } else {
-          // up to CB columns at once: independent float64 add chains
           for (int c0 = 0; c0 < b; c0 += CB) {
             const int cw = min(CB, b - c0);
-            RBO_CW_DISPATCH(sketch_row_f64, cw, skd + i + (size_t)c0 * d, d, ys + (size_t)c0 * TP, TP,
+            RBO_CW_DISPATCH(sketch_row_fix, cw, skd + i + (size_t)c0 * d, d,
+                            reinterpret_cast<const long long*>(ys) + (size_t)c0 * TP, TP, s_emax + c0,
                             e, cnt)
           }
         }
@@ -880,22 +914,22 @@ static int sm_count() {
   return g_num_sms;
 }
 
-static int g_smem_max[3] = {0, 0, 0};
+static int g_smem_max[6] = {0, 0, 0, 0, 0, 0};
 
 // Largest dynamic shared memory of the row-pass kernel (opt-in limit minus its
 // static shared memory); raises the kernel's limit to it on first use.
-template <int ARITH>
+template <int ARITH, bool SK>
 static int smem_limit() {
-  int& lim = g_smem_max[ARITH];
+  int& lim = g_smem_max[ARITH * 2 + (SK ? 1 : 0)];
   if (lim == 0) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     size_t stat = 0;
-    if (cudaFuncGetAttributes(&fa, rowpass_kernel<ARITH>) == cudaSuccess) stat = fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, rowpass_kernel<ARITH, SK>) == cudaSuccess) stat = fa.sharedSizeBytes;
     lim = optin - (int)stat - 64;
-    if (cudaFuncSetAttribute(rowpass_kernel<ARITH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(rowpass_kernel<ARITH, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              lim) != cudaSuccess) {
       cudaGetLastError();
       lim = 48 * 1024 - (int)stat;
@@ -904,14 +938,14 @@ static int smem_limit() {
   return lim;
 }
 
-template <int ARITH>
+template <int ARITH, bool SK>
 static int occupancy(int smem) {
-  long long key = (long long)smem * 4 + ARITH;
+  long long key = (long long)smem * 8 + ARITH * 2 + (SK ? 1 : 0);
   auto it = g_occ.find(key);
   if (it != g_occ.end()) return it->second;
   int nb = 0;
-  smem_limit<ARITH>();
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<ARITH>, NT, smem) !=
+  smem_limit<ARITH, SK>();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<ARITH, SK>, NT, smem) !=
       cudaSuccess) {
     cudaGetLastError();
     nb = 1;
@@ -974,7 +1008,8 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   }
   const int mixed = arith == 1 ? 1 : 0;
   if (dsk > 0) {
-    // sketch passes run on the tiles of the call's sketch schedule
+    // sketch passes run on the tiles of the call's sketch schedule, without a Gram
+    if (no > 0) return RBO_ERR_ARG;
     if (rp.sk.rec == nullptr || rp.sk.mcap != sketch_sched_mcap(rp.sk.T, dsk, rp.sk_zeta) ||
         rp.sk.rec_bytes != sketch_sched_rec_bytes(rp.sk.T, dsk, rp.sk_zeta))
       return RBO_ERR_ARG;
@@ -1019,11 +1054,16 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     if (smem <= 220 * 1024 || T == 16 || dsk > 0) break;
     T /= 2;
   }
-  const int limit = arith == 1 ? smem_limit<1>() : (arith == 2 ? smem_limit<2>() : smem_limit<0>());
+  const bool sk = dsk > 0;  // the scatter instance (no Gram: checked above)
+  const int limit = sk ? (arith == 1 ? smem_limit<1, true>() : smem_limit<0, true>())
+                       : (arith == 1 ? smem_limit<1, false>()
+                                     : (arith == 2 ? smem_limit<2, false>() : smem_limit<0, false>()));
   if ((long long)smem > limit) return RBO_ERR_ARG;
   const int ntiles = (int)((rp.n + T - 1) / T);
-  const int occ = arith == 1 ? occupancy<1>((int)smem)
-                             : (arith == 2 ? occupancy<2>((int)smem) : occupancy<0>((int)smem));
+  const int occ = sk ? (arith == 1 ? occupancy<1, true>((int)smem) : occupancy<0, true>((int)smem))
+                     : (arith == 1 ? occupancy<1, false>((int)smem)
+                                   : (arith == 2 ? occupancy<2, false>((int)smem)
+                                                 : occupancy<0, false>((int)smem)));
   int G = std::min(ntiles, occ * sm_count());
   if (rp.max_ctas > 0) G = std::min(G, rp.max_ctas);
   if (G < 1) G = 1;
@@ -1074,11 +1114,13 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   }
   ProfToken tok = prof_start(st);
   if (arith == 1)
-    rowpass_kernel<1><<<G, NT, smem, st>>>(P);
+    if (sk) rowpass_kernel<1, true><<<G, NT, smem, st>>>(P);
+    else rowpass_kernel<1, false><<<G, NT, smem, st>>>(P);
   else if (arith == 2)
-    rowpass_kernel<2><<<G, NT, smem, st>>>(P);
+    rowpass_kernel<2, false><<<G, NT, smem, st>>>(P);
   else
-    rowpass_kernel<0><<<G, NT, smem, st>>>(P);
+    if (sk) rowpass_kernel<0, true><<<G, NT, smem, st>>>(P);
+    else rowpass_kernel<0, false><<<G, NT, smem, st>>>(P);
   if (prof_on()) {
     // algorithmic traffic: every n-row column read once, written once
     const double nn = (double)rp.n, A = rp.a, B = rp.b;
