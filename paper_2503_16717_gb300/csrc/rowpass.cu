@@ -428,7 +428,7 @@ __device__ __forceinline__ void sketch_row_f32(float* acc, int d, const float* y
 // the kernel
 // ------------------------------------------------------------------------------------
 template <int ARITH, bool SK>
-__global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const __grid_constant__ PassDev P) {
+__global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_kernel(const __grid_constant__ PassDev P) {
   // ARITH 0: float64; 1: float32 for X^T Y' and the sketch (mixed precision);
   // 2: float32 pairs for the transform and the Gram, float64 for the sketch.
   // SK: the pass scatters a sparse sketch (and has no Gram); separate instances keep
