@@ -101,6 +101,47 @@ def newton_shifts(H: np.ndarray, s: int):
     return alpha, beta
 
 
+# --- Chebyshev basis (Sections 5 and 8 name it beside the Newton basis; Joubert and
+# Carey, Comput. Math. Appl. 24, 1992) ---------------------------------------------
+def chebyshev_ellipse(theta: np.ndarray):
+    """Ellipse enclosing the Ritz values ``theta`` (closed under conjugation): centre c
+    on the real axis at the midpoint of their real extent, semi-axes (a, b) =
+    t (a0, b0) with a0 half the real extent, b0 the largest |Im theta| and t >= 1 the
+    smallest factor that puts every value inside (t = 1 when all values are real:
+    the ellipse is the interval itself).  Returns (c, e2), e2 = a^2 - b^2 the
+    squared half focal distance (negative when the foci lie on the imaginary line)."""
+    theta = np.asarray(theta, dtype=np.complex128)
+    x, y = theta.real, np.abs(theta.imag)
+    c = 0.5 * (float(x.max()) + float(x.min()))
+    a0 = 0.5 * (float(x.max()) - float(x.min()))
+    b0 = float(y.max())
+    t2 = 1.0
+    for xi, yi in zip(x, y):
+        v = 0.0
+        if a0 > 0.0:
+            v += ((xi - c) / a0) ** 2
+        if b0 > 0.0:
+            v += (yi / b0) ** 2
+        t2 = max(t2, v)
+    return c, t2 * (a0 * a0 - b0 * b0)
+
+
+def chebyshev_shifts(H: np.ndarray, s: int):
+    """Recurrence of s Chebyshev-basis vectors for the ellipse (c, e2) enclosing the
+    eigenvalues of the square upper-Hessenberg H: p_k(z) = 2 (e/2)^k T_k((z - c)/e),
+    k >= 1 (T_k the Chebyshev polynomials of the first kind), which satisfy
+    p_1 = (z - c), p_2 = (z - c) p_1 - (e2/2), p_{k+1} = (z - c) p_k - (e2/4) p_{k-1};
+    in the form v_{i+1} = (Ahat - alpha_i) v_i + beta_i v_{i-1}: alpha_i = c,
+    beta_0 = 0, beta_1 = -e2/2, beta_i = -e2/4 (i >= 2)."""
+    c, e2 = chebyshev_ellipse(np.linalg.eigvals(H))
+    alpha = np.full(s, c)
+    beta = np.full(s, -0.25 * e2)
+    beta[0] = 0.0
+    if s > 1:
+        beta[1] = -0.5 * e2
+    return alpha, beta
+
+
 def mpk_newton(Ahat, u: np.ndarray, alpha: np.ndarray, beta: np.ndarray) -> np.ndarray:
     """Newton matrix-powers kernel: v_0 = u, v_{i+1} = (Ahat - alpha_i) v_i + beta_i v_{i-1}
     (beta_0 = 0); returns [v_1, ..., v_s].  alpha = beta = 0 is the monomial basis."""
@@ -152,12 +193,16 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
                 basis: str = "monomial") -> GmresResult:
     """s-step GMRES(m) with one-stage (RandCholQR or CholQR2 BCGS2) or two-stage
     (big panels of s_hat, preprocessed by RandBCGS2 or BCGS-PIP) block
-    orthogonalization.  basis = "newton": the first cycle is standard GMRES (panels
-    of one column), later cycles use the Newton basis with shifts from the first
-    cycle's Ritz values;
+    orthogonalization.  basis = "newton" / "chebyshev": the first cycle is standard
+    GMRES (panels of one column), later cycles use the Newton basis with shifts from
+    the first cycle's Ritz values, or the Chebyshev basis of the ellipse enclosing
+    them;
     since Ahat U = W + U B for the generators U of a panel (B bidiagonal with
-    alpha on the diagonal and -beta above it), the Hessenberg matrix becomes
+    alpha on the diagonal and -beta above it; the Chebyshev basis is the same
+    three-term form), the Hessenberg matrix becomes
     (Y + X B) X^{-1}."""
+    if basis not in ("monomial", "newton", "chebyshev"):
+        raise ValueError(f"unknown basis {basis!r}")
     if precond == "jacobi":
         Ahat, dinv = jacobi_scaled(A)
     else:
@@ -221,7 +266,7 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
         z = np.zeros(0)
         # Newton basis: the cycle that provides the Ritz values is standard GMRES
         # (panels of one column, one-stage)
-        sc = 1 if (basis == "newton" and cycle == 0) else s
+        sc = 1 if (basis != "monomial" and cycle == 0) else s
         try:
             while ncols < m + 1:
                 P = ncols
@@ -281,6 +326,8 @@ def sstep_gmres(A, b, x0=None, *, s: int, m: int, tol: float, s_hat: int | None 
         y = y + Qb[:, :k] @ z
         if basis == "newton" and cycle == 0:
             alpha, beta_s = newton_shifts(H[:k, :k], s)
+        elif basis == "chebyshev" and cycle == 0:
+            alpha, beta_s = chebyshev_shifts(H[:k, :k], s)
     res.iterations = its
     res.x = dinv * y
     return res

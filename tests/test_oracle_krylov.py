@@ -161,3 +161,99 @@ def test_newton_basis_is_better_conditioned():
     a, bt = krylov.newton_shifts(Hh[:40, :40], 10)
     cond = lambda V: np.linalg.cond(V / np.linalg.norm(V, axis=0))  # noqa: E731
     assert cond(krylov.mpk_newton(Ahat, u, a, bt)) < 1e-3 * cond(krylov.mpk(Ahat, u, 10))
+
+
+def test_chebyshev_recurrence_is_scaled_chebyshev_polynomials():
+    # the recurrence p_1 = z - c, p_2 = (z - c) p_1 - e2/2, p_{k+1} = (z - c) p_k - e2/4 p_{k-1}
+    # reproduces 2 (e/2)^k T_k((z - c)/e), evaluated here with numpy's Chebyshev series
+    # (complex e when the foci lie on the imaginary line)
+    from numpy.polynomial import chebyshev as C
+    z = np.linspace(-1.5, 3.5, 11)
+    for lam in ([0.2, 1.9, 0.7, 1.1], [-1.0, 3.0, 0.5]):
+        a, bt = krylov.chebyshev_shifts(np.diag(lam), 6)
+        c, e = 0.5 * (max(lam) + min(lam)), 0.5 * (max(lam) - min(lam))
+        # real spectrum: the ellipse is the interval [min, max] itself
+        assert np.allclose(a, c, rtol=0, atol=1e-15) and np.isclose(-bt[1] * 2, e * e)
+        V = krylov.mpk_newton(np.diag(z), np.ones_like(z), a, bt)
+        for k in range(1, 7):
+            ref = 2 * (e / 2) ** k * C.chebval((z - c) / e, [0] * k + [1])
+            assert np.allclose(V[:, k - 1], ref, rtol=1e-12, atol=1e-12)
+    # a single conjugate pair 2 +- 3i: a segment on the line Re z = 2 whose foci are
+    # the pair itself (e2 = -9)
+    a, bt = krylov.chebyshev_shifts(np.array([[2.0, -3.0], [3.0, 2.0]]), 4)
+    assert np.allclose(a, 2.0) and np.allclose(bt, [0.0, 4.5, 2.25, 2.25])
+    # complex points z = x + iy act as the real 2 x 2 blocks [[x, -y], [y, x]]; a real
+    # polynomial p maps the block's first unit vector to (Re p(z), Im p(z))
+    e = 3j
+    zc = np.array([2 + 3j, 2 - 3j, 2.5 + 1j, 0.3 - 0.2j])
+    D = np.zeros((8, 8))
+    for i, zz in enumerate(zc):
+        D[2 * i:2 * i + 2, 2 * i:2 * i + 2] = [[zz.real, -zz.imag], [zz.imag, zz.real]]
+    u = np.tile([1.0, 0.0], 4)
+    V = krylov.mpk_newton(D, u, a, bt)
+    for k in range(1, 5):
+        ref = 2 * (e / 2) ** k * C.chebval((zc - 2.0) / e, [0] * k + [1])
+        assert np.allclose(V[0::2, k - 1], ref.real, rtol=1e-12, atol=1e-12)
+        assert np.allclose(V[1::2, k - 1], ref.imag, rtol=1e-12, atol=1e-12)
+
+
+def test_chebyshev_ellipse_encloses_ritz_values():
+    # the ellipse with foci c +- sqrt(e2) and the aspect ratio of the values' bounding
+    # box contains every value, and the smallest such ellipse touches one of them
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        re = rng.standard_normal(4)
+        cz = rng.standard_normal(3) + 1j * rng.uniform(0.1, 2.0, 3)
+        theta = np.concatenate([re, cz, cz.conj()])
+        c, e2 = krylov.chebyshev_ellipse(theta)
+        a0 = 0.5 * (theta.real.max() - theta.real.min())
+        b0 = np.abs(theta.imag).max()
+        assert np.isclose(c, 0.5 * (theta.real.max() + theta.real.min()))
+        f = np.sqrt(complex(e2))
+        # semi-axes (a, b) with b / a = b0 / a0 and a^2 - b^2 = e2
+        a = np.sqrt(e2 / (1 - (b0 / a0) ** 2)) if abs(a0 - b0) > 1e-12 else None
+        if a is None or not np.isfinite(a):
+            continue
+        if e2 > 0:
+            sums = np.abs(theta - (c + f)) + np.abs(theta - (c - f))
+            assert np.all(sums <= 2 * a * (1 + 1e-12))
+            assert sums.max() >= 2 * a * (1 - 1e-12)
+        else:
+            # foci on the line Re z = c: the sum of distances is at most 2b
+            b = np.sqrt(a * a - e2)
+            sums = np.abs(theta - (c + f)) + np.abs(theta - (c - f))
+            assert np.all(sums <= 2 * b * (1 + 1e-12))
+            assert sums.max() >= 2 * b * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("nonsym", [False, True])
+def test_chebyshev_estimates_equal_householder_gmres(nonsym):
+    # the Chebyshev basis spans the same Krylov space: estimates equal Householder GMRES
+    A = synth.convdiff2d_csr(24, seed=1)[0] if nonsym else synth.laplace2d_csr(20)
+    b = synth.ones_rhs(A)
+    ref = dict(krylov.householder_gmres(A, b, m=20, tol=1e-11, max_restarts=3).estimates)
+    g = krylov.sstep_gmres(A, b, s=5, m=20, tol=1e-11, max_restarts=3, basis="chebyshev")
+    checked = [(it, est) for it, est in g.estimates if it in ref and it > 20]
+    assert len(checked) >= 2
+    for it, est in checked:
+        assert abs(est - ref[it]) <= 1e-9 * ref[it]
+
+
+def test_chebyshev_basis_is_better_conditioned():
+    A = synth.poisson3d_csr(12)
+    Ahat, _ = krylov.jacobi_scaled(A)
+    u = np.random.default_rng(3).standard_normal(Ahat.shape[0])
+    u /= np.linalg.norm(u)
+    Q = np.zeros((Ahat.shape[0], 41))
+    Hh = np.zeros((41, 40))
+    Q[:, 0] = u
+    for j in range(40):
+        w = Ahat @ Q[:, j]
+        for i in range(j + 1):
+            Hh[i, j] = Q[:, i] @ w
+            w -= Hh[i, j] * Q[:, i]
+        Hh[j + 1, j] = np.linalg.norm(w)
+        Q[:, j + 1] = w / Hh[j + 1, j]
+    a, bt = krylov.chebyshev_shifts(Hh[:40, :40], 10)
+    cond = lambda V: np.linalg.cond(V / np.linalg.norm(V, axis=0))  # noqa: E731
+    assert cond(krylov.mpk_newton(Ahat, u, a, bt)) < 1e-3 * cond(krylov.mpk(Ahat, u, 10))
