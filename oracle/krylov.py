@@ -104,36 +104,57 @@ def newton_shifts(H: np.ndarray, s: int):
 # --- Chebyshev basis (Sections 5 and 8 name it beside the Newton basis; Joubert and
 # Carey, Comput. Math. Appl. 24, 1992) ---------------------------------------------
 def chebyshev_ellipse(theta: np.ndarray):
-    """Ellipse enclosing the Ritz values ``theta`` (closed under conjugation): centre c
-    on the real axis at the midpoint of their real extent, semi-axes (a, b) =
-    t (a0, b0) with a0 half the real extent, b0 the largest |Im theta| and t >= 1 the
-    smallest factor that puts every value inside (t = 1 when all values are real:
-    the ellipse is the interval itself).  Returns (c, e2), e2 = a^2 - b^2 the
-    squared half focal distance (negative when the foci lie on the imaginary line)."""
+    """Ellipse enclosing the Ritz values ``theta`` (closed under conjugation), with its
+    centre c on the real axis at the midpoint of their real extent and its axes along
+    the real and imaginary directions: among those, the one of smallest capacity
+    (a + b)/2 (a, b the real and imaginary semi-axes).  For a real semi-axis a the
+    smallest enclosing b is b(a) = max_i y_i a / sqrt(a^2 - dx_i^2) (dx_i = Re theta_i - c,
+    y_i = |Im theta_i|); a + b(a) is convex on a > a0 (a0 half the real extent), so a is
+    found by bisection on the sign of its right derivative
+    1 - y_i dx_i^2 / (a^2 - dx_i^2)^(3/2) (i the maximising value).  Real values give
+    the interval [min, max] itself (b = 0); values on one vertical line give the
+    segment (a = 0).  Returns (c, a, b)."""
     theta = np.asarray(theta, dtype=np.complex128)
     x, y = theta.real, np.abs(theta.imag)
     c = 0.5 * (float(x.max()) + float(x.min()))
     a0 = 0.5 * (float(x.max()) - float(x.min()))
     b0 = float(y.max())
-    t2 = 1.0
-    for xi, yi in zip(x, y):
-        v = 0.0
-        if a0 > 0.0:
-            v += ((xi - c) / a0) ** 2
-        if b0 > 0.0:
-            v += (yi / b0) ** 2
-        t2 = max(t2, v)
-    return c, t2 * (a0 * a0 - b0 * b0)
+    if b0 == 0.0:
+        return c, a0, 0.0
+    if a0 == 0.0:
+        return c, 0.0, b0
+    dx, y = (x - c)[y > 0], y[y > 0]
+
+    def b_and_slope(a):
+        r = a * a - dx * dx
+        g = y * a / np.sqrt(r)
+        i = int(np.argmax(g))
+        return float(g[i]), 1.0 - y[i] * dx[i] ** 2 / r[i] ** 1.5
+
+    # the minimiser a* satisfies a* <= a* + b(a*) <= a1 + b(a1) for any a1 > a0
+    a1 = 2.0 * a0 + b0
+    lo, hi = a0, a1 + b_and_slope(a1)[0]
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if b_and_slope(mid)[1] < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return c, hi, b_and_slope(hi)[0]
 
 
 def chebyshev_shifts(H: np.ndarray, s: int):
-    """Recurrence of s Chebyshev-basis vectors for the ellipse (c, e2) enclosing the
-    eigenvalues of the square upper-Hessenberg H: p_k(z) = 2 (e/2)^k T_k((z - c)/e),
+    """Recurrence of s Chebyshev-basis vectors for the ellipse (c, a, b) enclosing the
+    eigenvalues of the square upper-Hessenberg H (``chebyshev_ellipse``), with
+    e2 = a^2 - b^2 its squared half focal distance: p_k(z) = 2 (e/2)^k T_k((z - c)/e),
     k >= 1 (T_k the Chebyshev polynomials of the first kind), which satisfy
     p_1 = (z - c), p_2 = (z - c) p_1 - (e2/2), p_{k+1} = (z - c) p_k - (e2/4) p_{k-1};
     in the form v_{i+1} = (Ahat - alpha_i) v_i + beta_i v_{i-1}: alpha_i = c,
     beta_0 = 0, beta_1 = -e2/2, beta_i = -e2/4 (i >= 2)."""
-    c, e2 = chebyshev_ellipse(np.linalg.eigvals(H))
+    c, a, b = chebyshev_ellipse(np.linalg.eigvals(H))
+    e2 = a * a - b * b
     alpha = np.full(s, c)
     beta = np.full(s, -0.25 * e2)
     beta[0] = 0.0

@@ -197,33 +197,44 @@ def test_chebyshev_recurrence_is_scaled_chebyshev_polynomials():
         assert np.allclose(V[1::2, k - 1], ref.imag, rtol=1e-12, atol=1e-12)
 
 
-def test_chebyshev_ellipse_encloses_ritz_values():
-    # the ellipse with foci c +- sqrt(e2) and the aspect ratio of the values' bounding
-    # box contains every value, and the smallest such ellipse touches one of them
+def test_chebyshev_ellipse_closed_forms():
+    # four corners c +- d +- iy: minimising a + y / sqrt(1 - d^2/a^2) gives
+    # a^2 = d^2 + (y d^2)^(2/3); the unit-square corners give the circle of radius sqrt 2
+    c, a, b = krylov.chebyshev_ellipse(np.array([1 + 1j, 1 - 1j, -1 + 1j, -1 - 1j]))
+    assert c == 0.0 and abs(a - np.sqrt(2)) < 1e-14 and abs(b - np.sqrt(2)) < 1e-14
+    for d, y in [(1.0, 0.5), (2.0, 0.1), (0.3, 2.0)]:
+        pts = np.array([0.7 + d + 1j * y, 0.7 + d - 1j * y, 0.7 - d + 1j * y, 0.7 - d - 1j * y])
+        c, a, b = krylov.chebyshev_ellipse(pts)
+        assert abs(c - 0.7) < 1e-15
+        assert abs(a * a - (d * d + (y * d * d) ** (2.0 / 3.0))) < 1e-13 * a * a
+        assert abs((d / a) ** 2 + (y / b) ** 2 - 1.0) < 1e-13     # corners on the ellipse
+    # a real spectrum with a vanishing conjugate pair tends to the interval (continuity)
+    for eps in (1e-3, 1e-6, 1e-9):
+        c, a, b = krylov.chebyshev_ellipse(np.array([0.1, 1.9, 1.9 + 1j * eps, 1.9 - 1j * eps]))
+        assert abs(a - 0.9) < 10 * eps ** (2 / 3) and b < 10 * eps ** (1 / 3)
+
+
+def test_chebyshev_ellipse_is_smallest_enclosing():
+    # brute force over the family (centre c, axis-aligned semi-axes on a grid): no
+    # ellipse that contains every Ritz value has a smaller capacity (a + b)/2, and the
+    # returned ellipse contains every value
     rng = np.random.default_rng(5)
-    for trial in range(20):
+    for trial in range(10):
         re = rng.standard_normal(4)
         cz = rng.standard_normal(3) + 1j * rng.uniform(0.1, 2.0, 3)
         theta = np.concatenate([re, cz, cz.conj()])
-        c, e2 = krylov.chebyshev_ellipse(theta)
-        a0 = 0.5 * (theta.real.max() - theta.real.min())
-        b0 = np.abs(theta.imag).max()
+        c, a, b = krylov.chebyshev_ellipse(theta)
         assert np.isclose(c, 0.5 * (theta.real.max() + theta.real.min()))
-        f = np.sqrt(complex(e2))
-        # semi-axes (a, b) with b / a = b0 / a0 and a^2 - b^2 = e2
-        a = np.sqrt(e2 / (1 - (b0 / a0) ** 2)) if abs(a0 - b0) > 1e-12 else None
-        if a is None or not np.isfinite(a):
-            continue
-        if e2 > 0:
-            sums = np.abs(theta - (c + f)) + np.abs(theta - (c - f))
-            assert np.all(sums <= 2 * a * (1 + 1e-12))
-            assert sums.max() >= 2 * a * (1 - 1e-12)
-        else:
-            # foci on the line Re z = c: the sum of distances is at most 2b
-            b = np.sqrt(a * a - e2)
-            sums = np.abs(theta - (c + f)) + np.abs(theta - (c - f))
-            assert np.all(sums <= 2 * b * (1 + 1e-12))
-            assert sums.max() >= 2 * b * (1 - 1e-12)
+        x, y = theta.real - c, theta.imag
+        assert np.all((x / a) ** 2 + (y / b) ** 2 <= 1 + 1e-9)
+        top = 3 * max(np.abs(x).max(), np.abs(y).max())
+        ga, gb = np.meshgrid(np.linspace(1e-3, top, 700), np.linspace(1e-3, top, 700))
+        inside = np.ones(ga.shape, dtype=bool)
+        for xi, yi in zip(x, y):
+            inside &= (xi / ga) ** 2 + (yi / gb) ** 2 <= 1
+        best = (ga + gb)[inside].min()
+        assert best >= (a + b) * (1 - 1e-9)
+        assert best <= (a + b) + 3 * top / 700
 
 
 @pytest.mark.parametrize("nonsym", [False, True])
