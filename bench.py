@@ -539,13 +539,13 @@ def run_learned(rbo, torch, args):
 def run_s_sweep(rbo, torch, Ad, bd, args):
     """Time to solution of the benchmark problem against the block size s (Sec. 8:
     sketching keeps larger s stable): one-stage and two-stage (s_hat = the smallest
-    multiple of s that is >= 20 and divides m), monomial and Newton basis."""
+    multiple of s that is >= 20 and divides m), monomial, Newton and Chebyshev basis."""
     out = []
     x = torch.zeros(Ad.n, dtype=torch.float64, device="cuda")
     for s_ in (5, 10, 15, 20, 30):
         sh = next(v for v in range(s_, M + 1, s_) if v >= 20 and M % v == 0)
         for s_hat in ((0, sh) if sh > s_ else (0,)):
-            for basis in (rbo.BASIS_MONOMIAL, rbo.BASIS_NEWTON):
+            for basis in (rbo.BASIS_MONOMIAL, rbo.BASIS_NEWTON, rbo.BASIS_CHEBYSHEV):
                 def go():
                     x.zero_()
                     return rbo.sstep_gmres(Ad, bd, x, s=s_, s_hat=s_hat, m=M, tol=TOL,
@@ -556,7 +556,8 @@ def run_s_sweep(rbo, torch, Ad, bd, args):
                 info = go()
                 torch.cuda.synchronize()
                 out.append({"s": s_, "s_hat": s_hat or s_, "scheme": "two" if s_hat > s_ else "one",
-                            "basis": "newton" if basis == rbo.BASIS_NEWTON else "monomial",
+                            "basis": {rbo.BASIS_MONOMIAL: "monomial", rbo.BASIS_NEWTON: "newton",
+                                      rbo.BASIS_CHEBYSHEV: "chebyshev"}[basis],
                             "status": info["status"], "iterations": info["iterations"],
                             "restarts": info["restarts"], "relres": info["relres"],
                             "s_per_solve": time.perf_counter() - t})

@@ -98,9 +98,12 @@ typedef struct rbo_opts {
 
 /* matrix-powers basis of s-step GMRES (rbo_opts.basis) */
 #define RBO_BASIS_MONOMIAL    0  /* v_{i+1} = A M v_i (the paper's choice)                */
-#define RBO_BASIS_NEWTON      1  /* first cycle monomial, then Newton steps with the Leja-
-                                    ordered Ritz values of the first cycle's Hessenberg
-                                    matrix as shifts (rbo_newton_shifts)                 */
+#define RBO_BASIS_NEWTON      1  /* first cycle standard GMRES, then Newton steps with the
+                                    Leja-ordered Ritz values of the first cycle's
+                                    Hessenberg matrix as shifts (rbo_newton_shifts)      */
+#define RBO_BASIS_CHEBYSHEV   2  /* first cycle standard GMRES, then the Chebyshev basis
+                                    of the ellipse enclosing its Ritz values
+                                    (rbo_chebyshev_shifts)                               */
 
 /* two-stage preprocessing of the panels of a big panel (rbo_opts.preproc) */
 #define RBO_PREPROC_RAND      0  /* RandBCGS2: sketch + sketched BCGS2-HH (Section 7.2)  */
@@ -264,6 +267,22 @@ int rbo_mpk_csr(const rbo_csr* A, const double* dscale, int32_t s, const double*
  * Errors: RBO_ERR_ARG, RBO_ERR_NOT_CONVERGED (QR iteration did not converge).      */
 int rbo_newton_shifts(const double* H, int64_t ld, int32_t k, int32_t s, double* alpha,
                       double* beta);
+
+/* Recurrence of the Chebyshev matrix-powers basis (Sections 5 and 8 name it beside the
+ * Newton basis; Joubert and Carey 1992), in the same form
+ *   v_{i+1} = (A - alpha_i) v_i + beta_i v_{i-1},  i = 0..s-1:
+ * v_k = p_k(A) v_0 with p_k(z) = 2 (e/2)^k T_k((z - c)/e) (T_k: Chebyshev polynomials of
+ * the first kind), i.e. alpha_i = c, beta_0 = 0, beta_1 = -e^2/2, beta_i = -e^2/4.  The
+ * ellipse (centre c on the real axis, half focal distance e; e^2 < 0 when the foci lie
+ * on the line Re z = c) encloses the eigenvalues of the k x k upper Hessenberg H (host,
+ * column-major, ld >= k): c is the midpoint of their real extent, the axes lie along
+ * the real and imaginary directions, and among those ellipses it has the smallest
+ * capacity (a + b)/2, a and b its semi-axes, e^2 = a^2 - b^2 (a real spectrum gives
+ * the interval of the eigenvalues).
+ * alpha, beta: caller-owned host arrays of s doubles.  Host-only (no GPU needed).
+ * Errors: RBO_ERR_ARG, RBO_ERR_NOT_CONVERGED (QR iteration did not converge).      */
+int rbo_chebyshev_shifts(const double* H, int64_t ld, int32_t k, int32_t s, double* alpha,
+                         double* beta);
 
 /* ---- s-step GMRES (Section 4, Figure 1) -------------------------------------------
  * (opts->preproc selects RandBCGS2 or BCGS-PIP for the two-stage panels)

@@ -51,6 +51,7 @@ PREPROC_RAND = 0
 PREPROC_PIP = 1
 BASIS_MONOMIAL = 0
 BASIS_NEWTON = 1
+BASIS_CHEBYSHEV = 2
 SKETCH_SPARSE_SIGN = 0
 SKETCH_GAUSSIAN = 1
 SKETCH_COUNT_GAUSS = 2
@@ -85,6 +86,7 @@ SIGNATURES = {
     "rbo_sketch_create": (C.c_int, [_i64, _i32, _i32, _u64, C.POINTER(_vp)]),
     "rbo_sketch_create_ex": (C.c_int, [_i64, _i32, _i32, _i32, _i32, _u64, C.POINTER(_vp)]),
     "rbo_newton_shifts": (C.c_int, [_dp, _i64, _i32, _i32, _dp, _dp]),
+    "rbo_chebyshev_shifts": (C.c_int, [_dp, _i64, _i32, _i32, _dp, _dp]),
     "rbo_sketch_destroy": (C.c_int, [_vp]),
     "rbo_sketch_entries": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "rbo_sketch_apply": (C.c_int, [_vp, _i64, _i32, _vp, _i64, _dp, _i32, _vp]),
@@ -366,6 +368,17 @@ def newton_shifts(H, s: int):
     a, b = np.zeros(s), np.zeros(s)
     _check(lib.rbo_newton_shifts(Hf.ctypes.data_as(C.c_void_p), k, k, s, a.ctypes.data_as(C.c_void_p),
                                  b.ctypes.data_as(C.c_void_p)), "newton_shifts")
+    return a, b
+
+
+def chebyshev_shifts(H, s: int):
+    """(alpha, beta) of the Chebyshev basis from the square upper-Hessenberg H (host)."""
+    Hf = np.asfortranarray(np.asarray(H, dtype=np.float64))
+    k = Hf.shape[0]
+    a, b = np.zeros(s), np.zeros(s)
+    _check(lib.rbo_chebyshev_shifts(Hf.ctypes.data_as(C.c_void_p), k, k, s,
+                                    a.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p)),
+           "chebyshev_shifts")
     return a, b
 
 

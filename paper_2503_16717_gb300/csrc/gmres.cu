@@ -161,10 +161,12 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   bool converged = false;
   double relres = INFINITY, est_rel = INFINITY;
   int cycle = 0, fallbacks = 0;
-  // Newton basis: shifts from the first cycle's Ritz values (monomial until then).
-  // The generators U of a panel satisfy A M U = W + U B with B bidiagonal (alpha on
-  // the diagonal, -beta above it), so the Hessenberg matrix is (Y + X B) X^{-1}.
-  const bool newton = opts && opts->basis == RBO_BASIS_NEWTON;
+  // Newton and Chebyshev bases: recurrence parameters from the first cycle's Ritz
+  // values (monomial until then).  The generators U of a panel satisfy
+  // A M U = W + U B with B bidiagonal (alpha on the diagonal, -beta above it), so the
+  // Hessenberg matrix is (Y + X B) X^{-1}.
+  const int basis = opts ? opts->basis : RBO_BASIS_MONOMIAL;
+  const bool poly_basis = basis != RBO_BASIS_MONOMIAL;
   std::vector<double> sh_a(s, 0.0), sh_b(s, 0.0);
   bool shifted = false;
   // output i of a panel from generators g_i (and g_{i-1})
@@ -240,10 +242,10 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
     int ncols = 1;
     int blk = 0;
     bool redo = false;
-    // Newton basis: the cycle that provides the Ritz values runs standard GMRES
-    // (panels of one column, one-stage), which does not depend on the conditioning
-    // of a monomial panel; later cycles use panels of s Newton vectors
-    const int sc = (newton && !shifted) ? 1 : s;
+    // Newton / Chebyshev basis: the cycle that provides the Ritz values runs standard
+    // GMRES (panels of one column, one-stage), which does not depend on the
+    // conditioning of a monomial panel; later cycles use panels of s shifted vectors
+    const int sc = (poly_basis && !shifted) ? 1 : s;
     while (ncols < m + 1) {
       const int P = ncols;
       if (!two || sc != s) {
@@ -367,9 +369,12 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
       if ((e = axpy_scaled_launch(n, w.dscale, w.t1, x, st))) return e;
       c.launches += 2;
     }
-    if (newton && !shifted && k >= 1) {
+    if (poly_basis && !shifted && k >= 1) {
       // Ritz values of the first cycle (kept monomial when the QR iteration fails)
-      if (newton_shifts(H.data(), ld, k, s, sh_a.data(), sh_b.data()) == RBO_OK) shifted = true;
+      const int r = basis == RBO_BASIS_CHEBYSHEV
+                        ? chebyshev_shifts(H.data(), ld, k, s, sh_a.data(), sh_b.data())
+                        : newton_shifts(H.data(), ld, k, s, sh_a.data(), sh_b.data());
+      if (r == RBO_OK) shifted = true;
     }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return RBO_ERR_CUDA;
@@ -427,7 +432,8 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
   if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 &&
       opts->precision != RBO_PREC_MIXED && opts->precision != RBO_PREC_DF64)
     code = RBO_ERR_ARG;
-  if (code == RBO_OK && opts && opts->basis != RBO_BASIS_MONOMIAL && opts->basis != RBO_BASIS_NEWTON)
+  if (code == RBO_OK && opts && opts->basis != RBO_BASIS_MONOMIAL && opts->basis != RBO_BASIS_NEWTON &&
+      opts->basis != RBO_BASIS_CHEBYSHEV)
     code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->intra != RBO_INTRA_RANDCHOLQR &&
       (opts->intra != RBO_INTRA_CHOLQR2 || s_hat > s))

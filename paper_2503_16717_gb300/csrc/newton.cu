@@ -1,8 +1,12 @@
-// Shifts of the Newton matrix-powers basis (host code): Ritz values of the Hessenberg
-// matrix of a GMRES cycle, ordered by the modified Leja ordering of Bai, Hu and Reichel
-// (IMA J. Numer. Anal. 14, 1994), turned into the real recurrence
-//   v_{i+1} = (A - alpha_i) v_i + beta_i v_{i-1}
-// (beta_i = (Im theta)^2 for the second value of a conjugate pair, else 0).
+// Parameters of the Newton and Chebyshev matrix-powers bases (host code), both as the
+// real three-term recurrence
+//   v_{i+1} = (A - alpha_i) v_i + beta_i v_{i-1}.
+// Newton: the Ritz values of the Hessenberg matrix of a GMRES cycle in the modified
+// Leja ordering of Bai, Hu and Reichel (IMA J. Numer. Anal. 14, 1994); beta_i =
+// (Im theta)^2 for the second value of a conjugate pair, else 0.
+// Chebyshev (Joubert and Carey, Comput. Math. Appl. 24, 1992): the scaled Chebyshev
+// polynomials 2 (e/2)^k T_k((z - c)/e) of an ellipse with centre c and half focal
+// distance e enclosing the Ritz values (e^2 < 0: foci on the line Re z = c).
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -175,7 +179,96 @@ int newton_shifts(const double* H, int64_t ld, int k, int s, double* alpha, doub
   return RBO_OK;
 }
 
+// Chebyshev basis: the ellipse has its centre c at the midpoint of the Ritz values'
+// real extent and its axes along the real and imaginary directions, and is the one of
+// smallest capacity (a + b)/2 that encloses every value.  For a real semi-axis a the
+// smallest b is b(a) = max_i y_i a / sqrt(a^2 - dx_i^2) (dx_i = Re theta_i - c,
+// y_i = |Im theta_i|); a + b(a) is convex for a above half the real extent a0, so a is
+// found by bisection on the sign of the right derivative 1 - y_i dx_i^2 / (a^2 -
+// dx_i^2)^(3/2), i the maximising value.  A real spectrum gives its interval (b = 0),
+// values on one vertical line the segment (a = 0).  With e2 = a^2 - b^2 the
+// recurrence is alpha_i = c, beta_0 = 0, beta_1 = -e2 / 2, beta_i = -e2 / 4 (i >= 2).
+static void chebyshev_ellipse(const std::vector<double>& wr, const std::vector<double>& wi,
+                              double& c, double& a, double& b) {
+  const size_t k = wr.size();
+  double xmin = wr[0], xmax = wr[0], b0 = 0.0;
+  for (size_t i = 0; i < k; ++i) {
+    xmin = std::min(xmin, wr[i]);
+    xmax = std::max(xmax, wr[i]);
+    b0 = std::max(b0, std::fabs(wi[i]));
+  }
+  c = 0.5 * (xmax + xmin);
+  const double a0 = 0.5 * (xmax - xmin);
+  if (b0 == 0.0) {
+    a = a0;
+    b = 0.0;
+    return;
+  }
+  if (a0 == 0.0) {
+    a = 0.0;
+    b = b0;
+    return;
+  }
+  std::vector<double> dx, y;
+  for (size_t i = 0; i < k; ++i)
+    if (wi[i] != 0.0) {
+      dx.push_back(wr[i] - c);
+      y.push_back(std::fabs(wi[i]));
+    }
+  // b(a) and the right derivative of a + b(a)
+  auto eval = [&](double av, double& slope) -> double {
+    double best = -1.0;
+    size_t bi = 0;
+    for (size_t i = 0; i < dx.size(); ++i) {
+      const double g = y[i] * av / std::sqrt(av * av - dx[i] * dx[i]);
+      if (g > best) {
+        best = g;
+        bi = i;
+      }
+    }
+    const double r = av * av - dx[bi] * dx[bi];
+    slope = 1.0 - y[bi] * dx[bi] * dx[bi] / (r * std::sqrt(r));
+    return best;
+  };
+  double slope;
+  const double a1 = 2.0 * a0 + b0;
+  double lo = a0, hi = a1 + eval(a1, slope);  // a* <= a* + b(a*) <= a1 + b(a1)
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    eval(mid, slope);
+    if (slope < 0.0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  a = hi;
+  b = eval(hi, slope);
+}
+
+int chebyshev_shifts(const double* H, int64_t ld, int k, int s, double* alpha, double* beta) {
+  if (!H || k < 1 || ld < k || s < 1 || !alpha || !beta) return RBO_ERR_ARG;
+  std::vector<double> A((size_t)k * k), wr, wi;
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < k; ++i) A[(size_t)i + (size_t)j * k] = (i <= j + 1) ? H[i + j * ld] : 0.0;
+  for (int i = 0; i < s; ++i) alpha[i] = beta[i] = 0.0;
+  if (!hessenberg_eig(A, k, wr, wi)) return RBO_ERR_NOT_CONVERGED;
+  double c, a, b;
+  chebyshev_ellipse(wr, wi, c, a, b);
+  const double e2 = a * a - b * b;
+  for (int i = 0; i < s; ++i) {
+    alpha[i] = c;
+    beta[i] = i == 0 ? 0.0 : (i == 1 ? -0.5 * e2 : -0.25 * e2);
+  }
+  return RBO_OK;
+}
+
 }  // namespace rbo
+
+extern "C" int rbo_chebyshev_shifts(const double* H, int64_t ld, int32_t k, int32_t s, double* alpha,
+                                    double* beta) {
+  return rbo::chebyshev_shifts(H, ld, k, s, alpha, beta);
+}
 
 extern "C" int rbo_newton_shifts(const double* H, int64_t ld, int32_t k, int32_t s, double* alpha,
                                  double* beta) {

@@ -245,6 +245,7 @@ int orth_ctx_alloc(OrthCtx& c, int pmax, int kmax, int64_t n);
 size_t orth_ctx_bytes(int pmax, int kmax, int d, int64_t n, int zeta, int type, int d_inner);
 // Newton-basis shifts from the k x k upper Hessenberg H (ld ld): alpha, beta (s each).
 int newton_shifts(const double* H, int64_t ld, int k, int s, double* alpha, double* beta);
+int chebyshev_shifts(const double* H, int64_t ld, int k, int s, double* alpha, double* beta);
 // Sketch fields of a row pass that applies the call's sketch.
 void set_sketch(RowPass& r, const OrthCtx& c);
 // Largest reduced-vector length of any pass for these sizes.

@@ -222,36 +222,44 @@ def test_gmres_with_gaussian_sketches(rbo, kind):
         assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6
 
 
+@pytest.mark.parametrize("basis", ["newton", "chebyshev"])
 @pytest.mark.parametrize("N,s,s_hat,m", [(16, 5, 0, 30), (16, 10, 0, 60), (16, 5, 10, 30),
                                          (16, 30, 0, 60), (16, 20, 60, 60)])
-def test_newton_basis_gmres_matches_oracle(rbo, N, s, s_hat, m):
-    # the Newton basis keeps large s usable: the first cycle is standard GMRES, later
-    # panels of s Newton vectors stay well conditioned (monomial s = 30 panels are
-    # numerically rank deficient)
+def test_newton_basis_gmres_matches_oracle(rbo, N, s, s_hat, m, basis):
+    # the Newton and Chebyshev bases keep large s usable: the first cycle is standard
+    # GMRES, later panels of s shifted vectors stay well conditioned (monomial s = 30
+    # panels are numerically rank deficient)
     import torch
     A = synth.poisson3d_csr(N)
     b = synth.ones_rhs(A)
+    code = rbo.BASIS_NEWTON if basis == "newton" else rbo.BASIS_CHEBYSHEV
     x, info = rbo.sstep_gmres(rbo.DeviceCSR.from_host(A), torch.from_numpy(b).cuda(), s=s,
-                              s_hat=s_hat, m=m, tol=1e-10, basis=rbo.BASIS_NEWTON)
+                              s_hat=s_hat, m=m, tol=1e-10, basis=code)
     scheme = "two" if s_hat > s else "one"
     ref = krylov.sstep_gmres(A, b, s=s, m=m, s_hat=(s_hat or None), scheme=scheme, tol=1e-10,
-                             basis="newton")
+                             basis=basis)
     assert info["status"] == 0 and info["converged"] == 1 and ref.converged
     gran = s_hat if s_hat > s else s
     assert abs(info["iterations"] - ref.iterations) <= gran
     assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-6
 
 
-def test_newton_basis_nonsymmetric(rbo):
-    # complex Ritz values: conjugate pairs in the real recurrence
+@pytest.mark.parametrize("basis", ["newton", "chebyshev"])
+def test_newton_basis_nonsymmetric(rbo, basis):
+    # complex Ritz values: conjugate pairs in the Newton recurrence, an ellipse (not an
+    # interval) for the Chebyshev basis
     import torch
     A, _ = synth.convdiff2d_csr(48, seed=1002)
     b = synth.ones_rhs(A)
     Ad = rbo.DeviceCSR.from_host(A)
     bd = torch.from_numpy(b).cuda()
-    x, info = rbo.sstep_gmres(Ad, bd, s=10, m=60, tol=1e-10, basis=rbo.BASIS_NEWTON)
-    ref = krylov.sstep_gmres(A, b, s=10, m=60, tol=1e-10, basis="newton")
+    code = rbo.BASIS_NEWTON if basis == "newton" else rbo.BASIS_CHEBYSHEV
+    x, info = rbo.sstep_gmres(Ad, bd, s=10, m=60, tol=1e-10, basis=code)
+    ref = krylov.sstep_gmres(A, b, s=10, m=60, tol=1e-10, basis=basis)
     assert info["converged"] == 1 and ref.converged
     assert abs(info["iterations"] - ref.iterations) <= 10
     r = b - A.to_scipy() @ x.cpu().numpy()
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    with pytest.raises(rbo.RboError) as e:
+        rbo.sstep_gmres(Ad, bd, s=10, m=60, tol=1e-10, basis=3, raise_on_error=True)
+    assert e.value.code == rbo.ERR_ARG

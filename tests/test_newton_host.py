@@ -1,6 +1,7 @@
-"""The Newton-basis shifts of the library (host code, no GPU needed) against the
-oracle's: Ritz values by the library's own Francis QR iteration versus numpy's
-eigenvalues, both in modified Leja order."""
+"""The Newton- and Chebyshev-basis recurrences of the library (host code, no GPU
+needed) against the oracle's: Ritz values by the library's own Francis QR iteration
+versus numpy's eigenvalues, then in modified Leja order (Newton) or through the
+smallest-capacity enclosing ellipse (Chebyshev)."""
 import numpy as np
 import pytest
 
@@ -46,3 +47,26 @@ def test_newton_shifts_of_arnoldi_matrix(rbo):
 def test_newton_shifts_bad_arguments(rbo):
     with pytest.raises(rbo.RboError):
         rbo.newton_shifts(np.zeros((0, 0)), 3)
+
+
+@pytest.mark.parametrize("k,s", [(1, 3), (2, 2), (3, 3), (10, 5), (30, 10), (61, 5), (128, 20)])
+def test_chebyshev_shifts_match_oracle(rbo, k, s):
+    rng = np.random.default_rng(100 + k)
+    for trial in range(4):
+        H = np.triu(rng.standard_normal((k, k)), -1)
+        a, b = rbo.chebyshev_shifts(H, s)
+        ao, bo = krylov.chebyshev_shifts(H, s)
+        scale = max(1.0, np.abs(ao).max(), np.abs(bo).max())
+        assert np.abs(a - ao).max() <= 1e-9 * scale
+        assert np.abs(b - bo).max() <= 1e-9 * scale
+
+
+def test_chebyshev_shifts_special_cases(rbo):
+    # real spectrum: the interval [min, max]; a single pair 2 +- 3i: the segment
+    a, b = rbo.chebyshev_shifts(np.diag([0.2, 1.9, 0.7]), 4)
+    assert np.allclose(a, 1.05) and np.allclose(b, [0.0, -0.5 * 0.85 ** 2, -0.25 * 0.85 ** 2,
+                                                     -0.25 * 0.85 ** 2])
+    a, b = rbo.chebyshev_shifts(np.array([[2.0, -3.0], [3.0, 2.0]]), 3)
+    assert np.allclose(a, 2.0) and np.allclose(b, [0.0, 4.5, 2.25])
+    with pytest.raises(rbo.RboError):
+        rbo.chebyshev_shifts(np.zeros((0, 0)), 3)
