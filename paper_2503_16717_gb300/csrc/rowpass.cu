@@ -767,11 +767,18 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
         // place as int64 fixed point (y' is not read again in a sketch pass)
         for (int c = tid; c < b; c += NT) s_emax[c] = 0;
         __syncthreads();
+        // (T a multiple of 32: the lanes of a warp share one column, so the warp takes
+        // its maximum first and one lane updates the shared value)
         for (int t = tid; t < b * T; t += NT) {
           const int c = t / T, r = t % T;
           const unsigned long long u = (unsigned long long)__double_as_longlong(ys[(size_t)c * TP + r]);
-          const int ex = (int)((u >> 52) & 0x7FF);
-          if (r < rows && ex != 0) atomicMax(&s_emax[c], ex);
+          int ex = r < rows ? (int)((u >> 52) & 0x7FF) : 0;
+          if ((T & 31) == 0) {
+            ex = __reduce_max_sync(0xffffffffu, ex);
+            if ((tid & 31) == 0 && ex != 0) atomicMax(&s_emax[c], ex);
+          } else if (ex != 0) {
+            atomicMax(&s_emax[c], ex);
+          }
         }
         __syncthreads();
         for (int t = tid; t < b * T; t += NT) {

@@ -35,15 +35,15 @@ def test_mpk_jacobi_scaled(rbo):
     assert np.allclose(V.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
 
 
-def _irregular_csr(seed):
+def _irregular_csr(seed, max_len=9, n=1037):
     """Short rows with empty rows, one row spanning several 256-entry chunks and a
-    row count that is not a multiple of 32."""
+    row count that is not a multiple of 32 (the short-row kernel: about 4.8 entries
+    per row at max_len = 9, 8.5 at max_len = 17)."""
     import scipy.sparse as sp
     rng = np.random.default_rng(seed)
-    n = 1037
-    lens = rng.integers(0, 9, size=n)
+    lens = rng.integers(0, max_len, size=n)
     lens[rng.choice(n, 40, replace=False)] = 0
-    lens[500], lens[31], lens[1036] = 700, 300, 12
+    lens[500], lens[31], lens[n - 1] = 700, 300, 12
     rows = np.repeat(np.arange(n), lens)
     cols = np.concatenate([rng.choice(n, k, replace=False) for k in lens])
     A = sp.csr_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(n, n))
@@ -51,10 +51,11 @@ def _irregular_csr(seed):
     return synth.CSR.from_scipy(A)
 
 
-def test_spmv_irregular_rows(rbo):
+@pytest.mark.parametrize("max_len,n", [(9, 1037), (17, 1037), (9, 70001), (3, 4099)])
+def test_spmv_irregular_rows(rbo, max_len, n):
     import torch
-    A = _irregular_csr(3)
-    assert 0 < A.nnz / A.n <= 12  # the short-row kernel
+    A = _irregular_csr(3, max_len, n)
+    assert 0 < A.nnz / A.n <= 12  # the short-row kernels
     u = np.random.default_rng(2).standard_normal(A.n)
     V = rbo.mpk_csr(rbo.DeviceCSR.from_host(A), torch.from_numpy(u).cuda(), 2)
     ref = krylov.mpk(A.to_scipy(), u, 2)
@@ -63,10 +64,15 @@ def test_spmv_irregular_rows(rbo):
         assert np.abs(got[:, i] - ref[:, i]).max() <= 1e-13 * np.abs(ref[:, i]).max()
 
 
-def test_spmv_column_out_of_range_is_reported(rbo):
+@pytest.mark.parametrize("max_len", [9, 17])
+@pytest.mark.parametrize("where", ["long", "short"])
+def test_spmv_column_out_of_range_is_reported(rbo, max_len, where):
+    # a bad index inside the long row (a group of several chunks) and inside a short row
     import torch
-    A = _irregular_csr(4)
-    A.col[A.rowptr[500] + 3] = A.n + 5  # one bad index inside the long row
+    A = _irregular_csr(4, max_len)
+    lens = np.diff(A.rowptr)
+    row = 500 if where == "long" else next(r for r in range(600, A.n) if 4 <= lens[r] <= 16)
+    A.col[A.rowptr[row] + 3] = A.n + 5
     with pytest.raises(rbo.RboError) as e:
         rbo.mpk_csr(rbo.DeviceCSR.from_host(A), torch.ones(A.n, dtype=torch.float64).cuda(), 1)
     assert e.value.code == rbo.ERR_ARG
