@@ -221,6 +221,7 @@ def run_ours(args):
     orth = run_orth(rbo, torch, args) if (rank == 0 and not args.no_orth) else None
     learned_res = run_learned(rbo, torch, args) if (rank == 0 and not args.no_learned) else None
     stress_res = run_stress(rbo, torch, args) if (rank == 0 and args.stress) else None
+    bases_res = run_stress_bases(rbo, torch, args) if (rank == 0 and args.stress_bases) else None
     sweep_res = run_s_sweep(rbo, torch, Ad, bd, args) if (rank == 0 and args.s_sweep) else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -253,6 +254,7 @@ def run_ours(args):
             "orth": orth,
             "learned": learned_res,
             "stress": stress_res,
+            "stress_bases": bases_res,
             "s_sweep": sweep_res,
             "cpu_baseline": cpu,
         }
@@ -637,6 +639,38 @@ def run_stress(rbo, torch, args):
     return out
 
 
+def run_stress_bases(rbo, torch, args):
+    """The stress problem (3D convection-diffusion, anisotropy (1, 1, 1e-3), Peclet 100,
+    seed 7, N^3 cells) solved by one-stage RandCholQR s-step GMRES(m=100) to 1e-10 with
+    the monomial, Newton and Chebyshev bases at s = 10, 20 and 25 (Section 4 names the
+    Newton and Chebyshev bases as the stabler matrix-powers bases)."""
+    import synth
+    N = args.stress_n
+    t0 = time.perf_counter()
+    Ah, meta = synth.convdiff3d_csr(N, seed=7)
+    A = rbo.DeviceCSR.from_host(Ah)
+    b = torch.from_numpy(synth.ones_rhs(Ah)).cuda()
+    out = {"N": N, "n": A.n, "nnz": A.nnz, "m": 100, "tol": 1e-10,
+           "generate_s": time.perf_counter() - t0, "runs": []}
+    del Ah
+    names = {rbo.BASIS_MONOMIAL: "monomial", rbo.BASIS_NEWTON: "newton",
+             rbo.BASIS_CHEBYSHEV: "chebyshev"}
+    for s_ in (10, 20, 25):
+        for basis in (rbo.BASIS_MONOMIAL, rbo.BASIS_NEWTON, rbo.BASIS_CHEBYSHEV):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, info = rbo.sstep_gmres(A, b, s=s_, m=100, tol=1e-10, basis=basis,
+                                      max_restarts=args.stress_restarts)
+            torch.cuda.synchronize()
+            out["runs"].append({"s": s_, "basis": names[basis], "status": info["status"],
+                                "converged": info["converged"], "iterations": info["iterations"],
+                                "restarts": info["restarts"], "relres": info["relres"],
+                                "s_per_solve": time.perf_counter() - t})
+    del A, b
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 def cpu_baseline(A, b, gpu_iterations, budget_cycles=2):
     """The oracle's one-stage s-step GMRES on the same problem for `budget_cycles`
@@ -715,6 +749,9 @@ def main():
                     help="also run the 3D convection-diffusion stress solve (s=10, s_hat=50, m=100)")
     ap.add_argument("--stress-n", type=int, default=256, help="grid points per side of the stress case")
     ap.add_argument("--stress-restarts", type=int, default=100)
+    ap.add_argument("--stress-bases", action="store_true",
+                    help="also solve the stress problem with the monomial, Newton and Chebyshev "
+                         "bases at s = 10, 20, 25")
     ap.add_argument("--s-sweep", action="store_true",
                     help="also time the workload's solves for s in 5, 10, 15, 20, 30")
     args = ap.parse_args()
