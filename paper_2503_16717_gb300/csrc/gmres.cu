@@ -126,16 +126,17 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   }
   // out = A M u: one SpMV with the column-scaled values (Jacobi), two SpMVs (M given),
   // or one SpMV with A (no preconditioner)
-  auto apply_op = [&](const double* u, double* out) -> int {
+  // out = A M u (+ the basis shift of `sh`, fused into the last SpMV)
+  auto apply_op = [&](const double* u, double* out, const SpmvShift& sh) -> int {
     int r;
     if (precond == 2) {
       if ((r = spmv_launch(Mop, nullptr, u, w.t2, ar->status, st))) return r;
-      if ((r = spmv_launch(Araw, nullptr, w.t2, out, ar->status, st))) return r;
+      if ((r = spmv_launch(Araw, nullptr, w.t2, out, ar->status, st, sh))) return r;
       c.launches += 2;
       return RBO_OK;
     }
     c.launches += 1;
-    return spmv_launch(Ahat, nullptr, u, out, ar->status, st);
+    return spmv_launch(Ahat, nullptr, u, out, ar->status, st, sh);
   };
   // ||b||
   {
@@ -171,9 +172,14 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   bool shifted = false;
   // output i of a panel from generators g_i (and g_{i-1})
   auto gen_step = [&](const double* gi, const double* gprev, double* out, int i) -> int {
-    int r = apply_op(gi, out);
-    if (r || !shifted) return r;
-    return shift_launch(n, out, gi, -sh_a[i], gprev, sh_b[i], st);
+    SpmvShift sh;
+    if (shifted) {
+      sh.u = gi;
+      sh.a = -sh_a[i];
+      sh.uprev = gprev;
+      sh.b = sh_b[i];
+    }
+    return apply_op(gi, out, sh);
   };
   // Y(:, c0 + i) += alpha_i X(:, c0 + i) - beta_i X(:, c0 + i - 1)
   auto shift_columns = [&](int c0) {

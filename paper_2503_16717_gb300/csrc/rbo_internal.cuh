@@ -195,10 +195,18 @@ struct CsrDev {
   const int32_t* col;
   const double* val;
 };
-// y = A (D x) (D = diag(dscale) when dscale != null)
+// Optional epilogue of an SpMV: y = (A x) + a u + b uprev (u null: none; uprev null or
+// b == 0: no third term), with the arithmetic of the separate shift pass (two fmas).
+struct SpmvShift {
+  const double* u = nullptr;
+  double a = 0.0;
+  const double* uprev = nullptr;
+  double b = 0.0;
+};
+// y = A (D x) (D = diag(dscale) when dscale != null), then the optional shift
 // Invalid indices are skipped and reported in `status` (may be null).
 int spmv_launch(const CsrDev& A, const double* dscale, const double* x, double* y,
-                DevStatus* status, cudaStream_t st);
+                DevStatus* status, cudaStream_t st, const SpmvShift& sh = SpmvShift());
 // r = b - A x  (A already scaled if needed)
 int residual_launch(const CsrDev& A, const double* b, const double* x, double* r, DevStatus* status,
                     cudaStream_t st);
@@ -211,9 +219,6 @@ int gemv_update_launch(int64_t n, int k, const double* Q, int64_t ldq, const dou
                        int accumulate, cudaStream_t st);
 // x += diag(ds) t  (ds null: x += t)
 int axpy_scaled_launch(int64_t n, const double* ds, const double* t, double* x, cudaStream_t st);
-// out += a u + b uprev (the Newton-basis step; uprev unused when b == 0)
-int shift_launch(int64_t n, double* out, const double* u, double a, const double* uprev, double b,
-                 cudaStream_t st);
 // mode 0: x = dscale .* y;  mode 1: x = y ./ dscale  (dscale null: copy)
 int scale_vec_launch(int64_t n, const double* dscale, const double* y, double* x, int mode,
                      cudaStream_t st);

@@ -10,6 +10,14 @@
 
 namespace rbo {
 
+// (A x)_r + a u_r + b uprev_r, in the order of the separate shift pass
+__device__ __forceinline__ double shifted(double s, const SpmvShift& sh, int64_t r) {
+  if (!sh.u) return s;
+  double v = fma(sh.a, sh.u[r], s);
+  if (sh.uprev) v = fma(sh.b, sh.uprev[r], v);
+  return v;
+}
+
 // Entries with a column index outside [0, n), or rows whose pointers leave [0, nnz],
 // are skipped and reported through the status word (RBO_ERR_ARG) instead of being
 // dereferenced.
@@ -21,7 +29,8 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, int64_t nnz,
                                                    const double* __restrict__ dscale,
                                                    const double* __restrict__ x,
                                                    const double* __restrict__ bvec,
-                                                   double* __restrict__ y, DevStatus* status) {
+                                                   double* __restrict__ y, DevStatus* status,
+                                                   SpmvShift sh) {
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gid / LPR;
   const int sub = (int)(gid % LPR);
@@ -44,7 +53,7 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, int64_t nnz,
   }
 #pragma unroll
   for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LPR);
-  if (row < n && sub == 0) y[row] = bvec ? (bvec[row] - s) : s;
+  if (row < n && sub == 0) y[row] = bvec ? (bvec[row] - s) : shifted(s, sh, row);
 }
 
 
@@ -64,7 +73,8 @@ __global__ void __launch_bounds__(256) spmv_stream_kernel(int64_t n, int64_t nnz
                                                           const double* __restrict__ dscale,
                                                           const double* __restrict__ x,
                                                           const double* __restrict__ bvec,
-                                                          double* __restrict__ y, DevStatus* status) {
+                                                          double* __restrict__ y, DevStatus* status,
+                                                          SpmvShift sh) {
   __shared__ double sv[8][SCH], sx[8][SCH];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ngroups = (n + 31) / 32;
@@ -141,39 +151,47 @@ __global__ void __launch_bounds__(256) spmv_stream_kernel(int64_t n, int64_t nnz
       }
     }
     s += s2;
-    if (r < n) y[r] = bvec ? (bvec[r] - s) : s;
+    if (r < n) y[r] = bvec ? (bvec[r] - s) : shifted(s, sh, r);
     beg = nbeg;
     end = nend;
   }
 }
 
 static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
-                               const double* b, double* y, DevStatus* status, cudaStream_t st);
+                               const double* b, double* y, DevStatus* status, cudaStream_t st,
+                               const SpmvShift& sh);
 
 template <int LPR>
 static void spmv_go(const CsrDev& A, const double* dscale, const double* x, const double* b,
-                    double* y, DevStatus* status, cudaStream_t st) {
+                    double* y, DevStatus* status, cudaStream_t st, const SpmvShift& sh) {
   const int64_t threads = A.n * LPR;
   const int64_t blocks = (threads + 255) / 256;
   spmv_kernel<LPR><<<(unsigned)blocks, 256, 0, st>>>(A.n, A.nnz, A.rowptr, A.col, A.val, dscale, x,
-                                                     b, y, status);
+                                                     b, y, status, sh);
 }
 
 static int spmv_dispatch(const CsrDev& A, const double* dscale, const double* x, const double* b,
-                         double* y, DevStatus* status, cudaStream_t st) {
+                         double* y, DevStatus* status, cudaStream_t st, const SpmvShift& sh) {
   if (A.n <= 0) return RBO_OK;
+  SpmvShift k = sh;
+  if (!k.u || b) k = SpmvShift();  // (a residual has no shift)
+  if (k.b == 0.0) k.uprev = nullptr;
   ProfToken tok = prof_start(st);
-  int e = spmv_dispatch_inner(A, dscale, x, b, y, status, st);
+  int e = spmv_dispatch_inner(A, dscale, x, b, y, status, st, k);
   // algorithmic bytes: values + column indices + row pointers, x and y once each
-  // (plus b and the scaling vector when used); 2 flops per stored entry
+  // (plus b, the scaling vector and the shift's vectors when used); 2 flops per
+  // stored entry (+2 per row and shift term)
   const double nn = (double)A.n, nz = (double)A.nnz;
+  const int terms = (k.u ? 1 : 0) + (k.uprev ? 1 : 0);
   prof_stop(tok, st, 1, 12.0 * nz + 4.0 * (nn + 1) + 16.0 * nn + (b ? 8.0 * nn : 0.0) +
-                            (dscale ? 8.0 * nn : 0.0), 2.0 * nz);
+                            (dscale ? 8.0 * nn : 0.0) + 8.0 * terms * nn,
+            2.0 * nz + 2.0 * terms * nn);
   return e;
 }
 
 static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const double* x,
-                               const double* b, double* y, DevStatus* status, cudaStream_t st) {
+                               const double* b, double* y, DevStatus* status, cudaStream_t st,
+                               const SpmvShift& sh) {
   const double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 0.0;
   if (avg <= 12.0) {
     int dev = 0, sms = 0;
@@ -181,22 +199,22 @@ static int spmv_dispatch_inner(const CsrDev& A, const double* dscale, const doub
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t blocks = std::min<int64_t>((A.n + 255) / 256, (int64_t)std::max(sms, 1) * 4);
     spmv_stream_kernel<<<(unsigned)blocks, 256, 0, st>>>(A.n, A.nnz, A.rowptr, A.col, A.val, dscale,
-                                                          x, b, y, status);
+                                                          x, b, y, status, sh);
   } else if (avg <= 24.0)
-    spmv_go<8>(A, dscale, x, b, y, status, st);
+    spmv_go<8>(A, dscale, x, b, y, status, st, sh);
   else
-    spmv_go<32>(A, dscale, x, b, y, status, st);
+    spmv_go<32>(A, dscale, x, b, y, status, st, sh);
   return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
 }
 
 int spmv_launch(const CsrDev& A, const double* dscale, const double* x, double* y, DevStatus* status,
-                cudaStream_t st) {
-  return spmv_dispatch(A, dscale, x, nullptr, y, status, st);
+                cudaStream_t st, const SpmvShift& sh) {
+  return spmv_dispatch(A, dscale, x, nullptr, y, status, st, sh);
 }
 
 int residual_launch(const CsrDev& A, const double* b, const double* x, double* r, DevStatus* status,
                     cudaStream_t st) {
-  return spmv_dispatch(A, nullptr, x, b, r, status, st);
+  return spmv_dispatch(A, nullptr, x, b, r, status, st, SpmvShift());
 }
 
 __global__ void scale_columns_kernel(int64_t n, int64_t nnz, const int32_t* __restrict__ col,
@@ -271,23 +289,6 @@ int axpy_scaled_launch(int64_t n, const double* ds, const double* t, double* x, 
 }
 
 // Newton-basis step: out += a u + b uprev (uprev may be null when b = 0)
-__global__ void shift_kernel(int64_t n, double* __restrict__ out, const double* __restrict__ u,
-                             double a, const double* __restrict__ uprev, double b) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double v = fma(a, u[i], out[i]);
-  if (uprev) v = fma(b, uprev[i], v);
-  out[i] = v;
-}
-
-int shift_launch(int64_t n, double* out, const double* u, double a, const double* uprev, double b,
-                 cudaStream_t st) {
-  if (n <= 0) return RBO_OK;
-  shift_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, out, u, a, b != 0.0 ? uprev : nullptr,
-                                                              b);
-  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
-}
-
 int gemv_update_launch(int64_t n, int k, const double* Q, int64_t ldq, const double* z, double* y,
                        int accumulate, cudaStream_t st) {
   if (n <= 0 || k <= 0) return RBO_OK;
