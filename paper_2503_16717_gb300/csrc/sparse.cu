@@ -1,11 +1,14 @@
 // CSR sparse kernels of the matrix-powers kernel (Section 4) and the small vector
 // kernels of the GMRES driver.
 //
-// SpMV: a group of LPR lanes per row (LPR = 4 for stencil-like rows of ~7
-// entries, 8/32 for denser rows); the lanes of a group read consecutive entries
-// of the row (coalesced col/val streams) and combine with shuffles in a fixed
-// order, so the result is deterministic.  The optional diagonal scaling D of the
-// right Jacobi preconditioner (A D x) is applied to the gathered x entries.
+// SpMV: rows of up to ~12 entries on average (stencils) go to a persistent kernel in
+// which each warp stages the entries of 32 consecutive rows in shared memory and
+// every lane runs its own row; denser rows use a group of LPR = 8 or 32 lanes per
+// row that read consecutive entries and combine with shuffles in a fixed order.
+// Every sum has a fixed order, so the result is deterministic.  The optional
+// diagonal scaling D of the right Jacobi preconditioner (A D x) is applied to the
+// gathered x entries; the optional shift terms of the Newton and Chebyshev bases
+// are added to each output row.
 #include "device_common.cuh"
 
 namespace rbo {
