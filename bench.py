@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -33,6 +34,17 @@ METRIC = "orth cols/s & HBM GB/s at ‖I−QᵀQ‖≤1e-13; s-step GMRES time t
 WORKLOAD = "s-step GMRES(m=60, s=5) one-stage + two-stage (s_hat=20), 3D Poisson 7-pt 100^3 (n=1e6), Jacobi, b=A*1, tol 1e-10"
 N_GRID, M, S, S_HAT, TOL = 100, 60, 5, 20, 1e-10
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+
+
+def max_over_ranks(value: float, dist=None, device="cuda") -> float:
+    """The largest `value` over all ranks of the process group (the slowest rank
+    decides a timing); `value` itself without a process group."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def peaks():
@@ -55,7 +67,7 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"rbo_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -152,10 +164,7 @@ def run_ours(args):
         barrier()
     ms = ev0.elapsed_time(ev1)
     gpu_launches = launches["n"]
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
     sec_per_solve = ms_per_step / 2.0 / 1e3
 
