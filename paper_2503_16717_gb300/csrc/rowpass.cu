@@ -20,6 +20,7 @@
 // sketched BCGS2-HH, R assembly) on the reduced values.
 #include <algorithm>
 #include <map>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "small_dense.cuh"
@@ -908,29 +909,38 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
 // ------------------------------------------------------------------------------------
 // host launcher
 // ------------------------------------------------------------------------------------
-static int g_num_sms = 0;
+// Per-device launch facts, cached on first use (guarded: calls for different devices
+// may come from different host threads).
+constexpr int MAX_DEV = 64;
+static std::mutex g_launch_mu;
+static int g_num_sms[MAX_DEV] = {};
+static int g_smem_max[MAX_DEV][6] = {};
 static std::map<long long, int> g_occ;
 
-static int sm_count() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
+static int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) dev = 0;
+  return dev;
 }
 
-static int g_smem_max[6] = {0, 0, 0, 0, 0, 0};
+static int sm_count() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  if (g_num_sms[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms[dev] = n > 0 ? n : 1;
+  }
+  return g_num_sms[dev];
+}
 
 // Largest dynamic shared memory of the row-pass kernel (opt-in limit minus its
-// static shared memory); raises the kernel's limit to it on first use.
+// static shared memory); raises the kernel's limit to it on first use on a device.
 template <int ARITH, bool SK>
-static int smem_limit() {
-  int& lim = g_smem_max[ARITH * 2 + (SK ? 1 : 0)];
+static int smem_limit_locked(int dev) {
+  int& lim = g_smem_max[dev][ARITH * 2 + (SK ? 1 : 0)];
   if (lim == 0) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
+    int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     size_t stat = 0;
@@ -946,12 +956,21 @@ static int smem_limit() {
 }
 
 template <int ARITH, bool SK>
+static int smem_limit() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  return smem_limit_locked<ARITH, SK>(dev);
+}
+
+template <int ARITH, bool SK>
 static int occupancy(int smem) {
-  long long key = (long long)smem * 8 + ARITH * 2 + (SK ? 1 : 0);
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  const long long key = ((long long)dev << 40) | ((long long)smem * 8 + ARITH * 2 + (SK ? 1 : 0));
   auto it = g_occ.find(key);
   if (it != g_occ.end()) return it->second;
   int nb = 0;
-  smem_limit<ARITH, SK>();
+  smem_limit_locked<ARITH, SK>(dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<ARITH, SK>, NT, smem) !=
       cudaSuccess) {
     cudaGetLastError();
