@@ -11,17 +11,22 @@ shares no code with the CUDA library.
 Modules
 -------
 sketch   sparse-sign sketch from the SplitMix64 stream (Section 3; "sparse
-         dimension reduction maps"), hash indices/signs and the sketch apply.
+         dimension reduction maps"), hash indices/signs and the sketch apply;
+         Gaussian and Count-Gauss sketches (Section 5.2).
 dense    small dense kernels: upper Cholesky with breakdown detection,
          Householder QR with non-negative diagonal, triangular solves.
 orth     BCGS, CholQR, CholQR2, RandHH, RandCholQR, one-stage BCGS2
-         (Figures 2-4, Section 5) and the two-stage scheme with RandBCGS2
-         preprocessing (Figures 5-7, Section 7, Appendix).
+         (Figures 2-4, Section 5) and the two-stage scheme with RandBCGS2 or
+         BCGS-PIP preprocessing (Figures 5-7, Section 7, Appendix).
 metrics  ||I - Q^T Q||_2 and ||V - QR||_2 / ||V||_2 evaluated in extended
          precision (equations (1), (2)-(3)).
-krylov   CSR SpMV, monomial matrix-powers kernel, s-step GMRES (Figure 1,
-         Section 4) and Householder-Arnoldi GMRES (Walker 1988) as the
-         brute-force reference.
+krylov   CSR SpMV, monomial, Newton (Leja-ordered Ritz values) and Chebyshev
+         (smallest-capacity ellipse) matrix-powers bases, s-step GMRES
+         (Figure 1, Section 4) and Householder-Arnoldi GMRES (Walker 1988) as
+         the brute-force reference.
+gnn      the learned sparse-approximate-inverse preconditioner of the workload
+         (not in the paper): graph network, loss, gradient, Adam, and the
+         classical SPAI minimiser as its pin.
 
 Parity status: every function has a pin in ``tests/test_oracle_*.py``
 (closed forms, library special cases, paper-stated invariants).  The
