@@ -73,3 +73,38 @@ def test_host_only_calls(pkg):
         pkg.sketch_create(1000, 4, 8, 42)   # zeta > d
     with pytest.raises(pkg.RboError):
         pkg.sketch_create(1000, 244, 17, 42)  # zeta too large
+
+
+def test_c_program_links_and_calls_host_entry_points(pkg, tmp_path):
+    # the header compiles as strict C99 and a C program links against the library
+    # and runs its host-only entry points (no GPU needed)
+    prog = tmp_path / "host.c"
+    prog.write_text(r'''
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+#include "rbo.h"
+int main(void) {
+  double H[4] = {2.0, 3.0, -3.0, 2.0};  /* eigenvalues 2 +- 3i, column-major */
+  double a[3], b[3];
+  rbo_sketch sk = NULL;
+  if (strncmp(rbo_version(), "rbo", 3) != 0) return 1;
+  if (rbo_newton_shifts(H, 2, 2, 2, a, b) != RBO_OK) return 2;
+  if (fabs(a[0] - 2.0) > 1e-12 || fabs(a[1] - 2.0) > 1e-12 || fabs(b[1] - 9.0) > 1e-10) return 3;
+  if (rbo_chebyshev_shifts(H, 2, 2, 3, a, b) != RBO_OK) return 4;
+  if (fabs(a[2] - 2.0) > 1e-12 || fabs(b[1] - 4.5) > 1e-10 || fabs(b[2] - 2.25) > 1e-10) return 5;
+  if (rbo_newton_shifts(H, 2, 0, 2, a, b) != RBO_ERR_ARG) return 6;
+  if (rbo_sketch_create(1000, 244, 8, 42, &sk) != RBO_OK || sk == NULL) return 7;
+  if (rbo_sketch_destroy(sk) != RBO_OK) return 8;
+  printf("ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "host"
+    libdir = os.path.dirname(pkg.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe),
+                    "-L", libdir, "-l:" + os.path.basename(pkg.LIB_PATH),
+                    "-Wl,-rpath," + libdir, "-lm"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
