@@ -383,6 +383,38 @@ def chebyshev_shifts(H, s: int):
 
 
 # ---- learned SPAI preconditioner -----------------------------------------------------------
+GNN_FILE_MAGIC = b"RBOGNN1\0"
+
+
+def gnn_write(path, theta, seed: int) -> None:
+    """Checkpoint of the network's weights: the 8-byte magic, the parameter count
+    (uint32) and the creation seed (uint64), little-endian, then the float32 master
+    weights in the library's parameter order.  The BF16 copy the kernels use is
+    rounded from them when they are loaded."""
+    th = np.ascontiguousarray(theta, dtype="<f4").ravel()
+    with open(path, "wb") as f:
+        f.write(GNN_FILE_MAGIC)
+        f.write(np.array([th.size], dtype="<u4").tobytes())
+        f.write(np.array([seed], dtype="<u8").tobytes())
+        f.write(th.tobytes())
+
+
+def gnn_read(path):
+    """(weights, seed) of a checkpoint written by ``gnn_write``; ValueError for a file
+    that is not one or whose parameter count differs from this library's network."""
+    with open(path, "rb") as f:
+        raw = f.read()
+    if len(raw) < 20 or raw[:8] != GNN_FILE_MAGIC:
+        raise ValueError(f"{path}: not a network checkpoint")
+    count = int(np.frombuffer(raw[8:12], dtype="<u4")[0])
+    seed = int(np.frombuffer(raw[12:20], dtype="<u8")[0])
+    if count != lib.rbo_gnn_param_count():
+        raise ValueError(f"{path}: {count} parameters, the network has {lib.rbo_gnn_param_count()}")
+    if len(raw) != 20 + 4 * count:
+        raise ValueError(f"{path}: truncated or oversized checkpoint")
+    return np.frombuffer(raw[20:], dtype="<f4").astype(np.float32), seed
+
+
 class GNN:
     """Handle of the learned sparse-approximate-inverse network (BF16 weights, FP32
     master weights and Adam state on the device)."""
@@ -391,7 +423,20 @@ class GNN:
         h = C.c_void_p()
         _check(lib.rbo_gnn_create(seed, C.byref(h)), "gnn_create")
         self.handle = h
+        self.seed = seed
         self.nparam = lib.rbo_gnn_param_count()
+
+    def save(self, path) -> None:
+        """Write the weights (not the optimiser state) to a checkpoint file."""
+        gnn_write(path, self.get_params(), self.seed)
+
+    @classmethod
+    def load(cls, path) -> "GNN":
+        """A network with the weights of a checkpoint file."""
+        theta, seed = gnn_read(path)
+        net = cls(seed)
+        net.set_params(theta)
+        return net
 
     def __del__(self):
         h = getattr(self, "handle", None)

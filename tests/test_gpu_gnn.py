@@ -43,6 +43,20 @@ def test_forward_matches_oracle(rbo, problem):
     assert np.abs(M - ref).max() <= 1e-4 * np.abs(ref).max()
 
 
+def test_checkpoint_round_trip(rbo, problem, tmp_path):
+    # weights written by save() and read back by load() give the same network
+    A, _ = problem
+    net = rbo.GNN(seed=4)
+    net.set_params(_theta(13))
+    path = tmp_path / "net.bin"
+    net.save(path)
+    net2 = rbo.GNN.load(path)
+    assert net2.seed == 4
+    assert np.array_equal(net2.get_params(), net.get_params())
+    Ad = rbo.DeviceCSR.from_host(A)
+    assert np.array_equal(net2.infer(Ad).cpu().numpy(), net.infer(Ad).cpu().numpy())
+
+
 def test_loss_and_gradient_match_oracle(rbo, problem):
     import torch
     A, G = problem
