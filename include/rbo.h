@@ -292,7 +292,10 @@ int rbo_chebyshev_shifts(const double* H, int64_t ld, int32_t k, int32_t s, doub
  * randomized BCGS2; s < s_hat (s | s_hat | m): two-stage with RandBCGS2.
  * opts->intra = RBO_INTRA_CHOLQR2 runs the one-stage scheme with CholQR2 instead of
  * RandCholQR (the deterministic baseline, which breaks down on ill-conditioned
- * monomial panels).
+ * monomial panels).  opts->basis selects the matrix-powers basis: monomial (the
+ * paper's), or Newton / Chebyshev, whose first restart cycle runs standard GMRES to
+ * obtain the Ritz values (rbo_newton_shifts, rbo_chebyshev_shifts) and whose later
+ * panels use the shifted three-term recurrence (H = (Y + X B) X^-1).
  * The sketch has d = 4 (m + 1) rows, zeta = 8, seed 42 unless `sk` is given.
  * Converged when ||b - A x||_2 <= tol ||b||_2 (true residual).
  * Errors: RBO_ERR_ARG, RBO_ERR_NOT_CONVERGED, RBO_ERR_CHOL_BREAKDOWN, RBO_ERR_CUDA,
