@@ -24,6 +24,9 @@
  *   - Every call returns RBO_OK (0) or a negative RBO_ERR_* code; no call
  *     throws or aborts.  On an error the contents of the in/out arrays are
  *     unspecified.
+ *   - The library caches per-device state (the workspace arena, launch facts,
+ *     device addresses of static arrays); it must not be used on a device across
+ *     a cudaDeviceReset of that device.
  */
 #ifndef RBO_H
 #define RBO_H
@@ -200,11 +203,13 @@ int rbo_gram(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, cons
  * device array (RBO_NOALLOC_SCRATCH_BYTES) that every GPU loading the library keeps
  * until the process exits.  Limits: a <= 128, b <= 64, a * b <= 2048 (larger shapes
  * return RBO_ERR_ARG).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's contents
- * (each call re-zeroes the counters it needs), so calls that overlap on the GPU --
- * different streams or host threads at the same time -- race and must be
- * serialised by the caller.  Synchronises `stream` once to read the status word.
+ * address (cudaGetSymbolAddress) and caches it for that device; that first call
+ * should come before any stream capture begins.  All calls share the array and it
+ * keeps the last call's contents (each call re-zeroes the counters it needs), so
+ * calls that overlap on the GPU -- different streams or host threads at the same
+ * time -- race and must be serialised by the caller.  Every call ends with a
+ * device-to-host copy of the status word and a synchronisation of `stream`.  The
+ * cached address does not survive a cudaDeviceReset of that device.
  * Errors: RBO_ERR_ARG, RBO_ERR_NO_DEVICE, RBO_ERR_TIMEOUT, RBO_ERR_CUDA.            */
 int rbo_gram_noalloc(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b,
                      const double* Y, int64_t ldy, double* C, void* stream);

@@ -32,7 +32,8 @@ unsigned char* g_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array for the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once per
-// device, with that device current, and cached.
+// device, with that device current, and cached (a cudaDeviceReset reloads the
+// module and invalidates the cached address; the library is not used across one).
 int scratch_address(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

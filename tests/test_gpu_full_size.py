@@ -69,3 +69,39 @@ def test_full_size_mixed_at_kappa_1e4(rbo):
     import torch
     V0 = synth.glued_blocks_torch(N, 12, 5, 1e4, seed=2, v0=True, device="cuda")
     _check(rbo, torch, V0, "two", rbo.PREC_MIXED, 1e4)
+
+
+# ---- s-step GMRES at the benchmark's size -------------------------------------------------
+@pytest.mark.parametrize("scheme,s_hat", [("one_stage", 0), ("two_stage", 20)])
+def test_gmres_poisson100_matches_oracle_golden(rbo, scheme, s_hat):
+    """s-step GMRES(m=60, s=5) on the 3D Poisson 100^3 workload (n = 1e6, Jacobi,
+    b = A 1) in the launch configuration the benchmark times, against the oracle's own
+    full solves (tests/golden/gmres_poisson100.json, written by the oracle-only script
+    beside it): converged to 1e-10 within one check granularity (s one-stage, s_hat
+    two-stage) of the oracle's iteration count, and x = 1 to the accuracy the residual
+    implies."""
+    import json
+    import os
+    import torch
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gmres_poisson100.json")) as f:
+        gold = json.load(f)[scheme]
+    A = synth.poisson3d_csr(100)
+    b = synth.ones_rhs(A)
+    Ad = rbo.DeviceCSR.from_host(A)
+    bd = torch.from_numpy(b).cuda()
+    x, info = rbo.sstep_gmres(Ad, bd, s=5, s_hat=s_hat, m=60, tol=1e-10)
+    assert info["status"] == 0 and info["converged"] == 1, info
+    gran = 5 if s_hat == 0 else s_hat
+    assert abs(info["iterations"] - gold["iterations"]) <= gran, (info["iterations"], gold["iterations"])
+    assert info["relres"] <= 1e-10
+    # the true residual, recomputed here with scipy on the host
+    xh = x.cpu().numpy()
+    r = b - A.to_scipy() @ xh
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b) * 1.0001
+    assert np.abs(xh - 1.0).max() <= 1e-6
+    # the true relative residual at every restart agrees with the oracle's history
+    gh = dict((int(i), v) for i, v in gold["history"])
+    common = [(i, v) for i, v in info["history"] if i in gh and i > 0]
+    assert len(common) >= 10
+    for i, v in common:
+        assert abs(v - gh[i]) <= 1e-6 * gh[i], (i, v, gh[i])
