@@ -68,6 +68,16 @@ extern "C" {
                               the sketch and the small factors in float64.  Only steps
                               that cannot reach the backward error ||V - QR|| are
                               moved off the float64 pipe                              */
+#define RBO_PREC_OZAKI  3  /* float64 data and results; the Gram matrices of the BCGS and
+                              CholQR reductions (passes with at most 64 columns of [X Y']
+                              and 8 of Y', no projection) are computed on the bf16 tensor
+                              cores from exact integer products: per tile of 128 rows
+                              every value is scaled by its column's largest power of two
+                              to a 55-bit integer, split into 7 balanced 8-bit digits
+                              (each exact in bf16), the digit products are summed exactly
+                              in float32 and the pairs of digit levels I + J <= 6 are
+                              combined in 64/128-bit integers (Ozaki, Ogita, Oishi and
+                              Rump 2012); every other step as RBO_PREC_FP64            */
 
 /* ---- intra-block choice (one-stage) ----------------------------------------- */
 #define RBO_INTRA_RANDCHOLQR 0  /* RandCholQR (Figure 4b)                                */
@@ -191,6 +201,11 @@ int rbo_sketch_apply(rbo_sketch sk, int64_t n, int32_t k, const double* W, int64
  * (fixed-order cross-CTA tree).                                                   */
 int rbo_gram(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, const double* Y,
              int64_t ldy, double* C, void* stream);
+/* The same Gram in a given precision: RBO_PREC_FP64 (as rbo_gram) or RBO_PREC_OZAKI (the
+ * tensor-core digit products; a <= 64 and b <= 8, RBO_ERR_ARG otherwise).  A column
+ * holding a non-finite value gives NaN in its row or column of C.                  */
+int rbo_gram_ex(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, const double* Y,
+                int64_t ldy, double* C, int32_t precision, void* stream);
 
 /* ---- tall-skinny Gram without allocation -------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that cannot
@@ -362,6 +377,8 @@ int rbo_gnn_train_step(rbo_gnn g, const rbo_csr* A, const double* R, int32_t nr,
 #define RBO_PROF_ROWPASS 0  /* the fused tall-skinny row pass (Gram / update / TRSM / sketch) */
 #define RBO_PROF_SPMV    1  /* CSR SpMV of the matrix-powers kernel and residuals           */
 #define RBO_PROF_VECTOR  2  /* small vector kernels (Jacobi setup, x update, scaling)       */
+#define RBO_PROF_OZAKI   3  /* the tensor-core Gram passes of RBO_PREC_OZAKI (also counted
+                               by role below)                                           */
 /* Row passes are also accumulated by role under kind RBO_PROF_PASS + role:
  * 1..6 one-stage P1 (Gram C1), P2 (update + sketch), P3 (TRSM R_hat + Gram),
  * P4 (TRSM R' + Gram C2), P5 (re-orthogonalization update + Gram), P6 (final TRSM);

@@ -8,6 +8,8 @@
   written out, returning R with a non-negative diagonal (the normalisation of
   the QR factorisation in the caption of Figure 1) and optionally the thin Q.
 * ``solve_right_upper``: X = W R^{-1} (the TRSM of CholQR and RandHH).
+* ``gram``: C = X^T Y, the reduction of BCGS and CholQR, with products and sums in
+  numpy's extended ``longdouble`` type (the reference for Gram kernels).
 """
 from __future__ import annotations
 
@@ -78,3 +80,12 @@ def solve_right_upper(W: np.ndarray, R: np.ndarray) -> np.ndarray:
         return W.copy()
     # X R = W  <=>  R^T X^T = W^T
     return sla.solve_triangular(R, W.T, trans="T", lower=False).T
+
+
+def gram(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """C = X^T Y (Section 9 lists it as the reduction of BCGS, C = Q^T W, and of
+    CholQR, G = W^T W).  Products and sums in extended precision (longdouble), rounded
+    to float64 once, so its own error is far below float64 rounding."""
+    Xl = np.asarray(X, dtype=np.longdouble)
+    Yl = np.asarray(Y, dtype=np.longdouble)
+    return (Xl.T @ Yl).astype(np.float64)

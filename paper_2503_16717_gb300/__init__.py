@@ -44,6 +44,7 @@ ERR_LOST_ORTHOGONALITY = -9
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_DF64 = 2
+PREC_OZAKI = 3   # Gram passes as exact digit products on the bf16 tensor cores
 INTRA_RANDCHOLQR = 0
 INTRA_CHOLQR2 = 1
 STAGE_NAMES = {0: "", 1: "v0", 2: "intra", 3: "intra2", 4: "final", 5: "bigpanel", 6: "preproc"}
@@ -91,6 +92,7 @@ SIGNATURES = {
     "rbo_sketch_entries": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "rbo_sketch_apply": (C.c_int, [_vp, _i64, _i32, _vp, _i64, _dp, _i32, _vp]),
     "rbo_gram": (C.c_int, [_i64, _i32, _vp, _i64, _i32, _vp, _i64, _dp, _vp]),
+    "rbo_gram_ex": (C.c_int, [_i64, _i32, _vp, _i64, _i32, _vp, _i64, _dp, _i32, _vp]),
     "rbo_gram_noalloc": (C.c_int, [_i64, _i32, _vp, _i64, _i32, _vp, _i64, _vp, _vp]),
     "rbo_block_orth_one_stage": (C.c_int, [_vp, _i64, _i32, _i32, _vp, _i64, _dp, _i64,
                                            C.POINTER(Opts), C.POINTER(Info), _vp]),
@@ -231,14 +233,16 @@ def sketch_apply(sk: Sketch, W, precision: int = PREC_FP64) -> np.ndarray:
     return out.T
 
 
-def gram(X, Y) -> np.ndarray:
-    """X^T Y for column-major CUDA tensors (deterministic tree reduction)."""
+def gram(X, Y, precision: int = PREC_FP64) -> np.ndarray:
+    """X^T Y for column-major CUDA tensors (deterministic tree reduction); precision
+    PREC_FP64 or PREC_OZAKI (tensor-core digit products)."""
     px, n, a, ldx = _mat(X, "X")
     py, n2, b, ldy = _mat(Y, "Y")
     if n2 != n:
         raise ValueError("row counts differ")
     out = np.zeros((b, a), dtype=np.float64)
-    _check(lib.rbo_gram(n, a, px, ldx, b, py, ldy, out.ctypes.data_as(C.c_void_p), _stream()), "gram")
+    _check(lib.rbo_gram_ex(n, a, px, ldx, b, py, ldy, out.ctypes.data_as(C.c_void_p), precision,
+                           _stream()), "gram")
     return out.T
 
 
@@ -481,7 +485,7 @@ class GNN:
         return loss.value
 
 
-PROF_ROWPASS, PROF_SPMV, PROF_VECTOR = 0, 1, 2
+PROF_ROWPASS, PROF_SPMV, PROF_VECTOR, PROF_OZAKI = 0, 1, 2, 3
 
 
 def profile_enable(on: bool = True):

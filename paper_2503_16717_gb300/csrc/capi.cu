@@ -282,9 +282,16 @@ int rbo_sketch_apply(rbo_sketch sk, int64_t n, int32_t k, const double* W, int64
 
 int rbo_gram(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, const double* Y,
              int64_t ldy, double* C, void* stream) {
+  return rbo_gram_ex(n, a, X, ldx, b, Y, ldy, C, RBO_PREC_FP64, stream);
+}
+
+int rbo_gram_ex(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, const double* Y,
+                int64_t ldy, double* C, int32_t precision, void* stream) {
   if (n < 1 || a < 1 || a > 128 || b < 1 || b > 64 || !X || !Y || !C || ldx < n || ldy < n ||
       a * b > 8192)
     return RBO_ERR_ARG;
+  if (precision != RBO_PREC_FP64 && precision != RBO_PREC_OZAKI) return RBO_ERR_ARG;
+  if (precision == RBO_PREC_OZAKI && (a > 64 || b > 8)) return RBO_ERR_ARG;
   int e = check_device();
   if (e) return e;
   cudaStream_t st = (cudaStream_t)stream;
@@ -296,6 +303,7 @@ int rbo_gram(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, cons
   RowPass r;
   r.n = n; r.X = X; r.ldx = ldx; r.a = a; r.Y = const_cast<double*>(Y); r.ldy = ldy; r.b = b;
   r.acc_x = 1;
+  r.ozaki = precision == RBO_PREC_OZAKI ? 1 : 0;
   r.epi.op = EPI_STORE; r.epi.out = dout; r.epi.out_ld = a;
   int launches = 0;
   if ((e = rowpass_launch(r, ar, st, &launches))) return e;
@@ -313,7 +321,7 @@ static int orth_common_checks(int64_t n, int32_t ncols, int32_t s, double* V, in
   if (n < ncols) return RBO_ERR_ARG;
   if ((ncols - v0) % s != 0) return RBO_ERR_ARG;
   if (opts && (opts->precision != RBO_PREC_FP64 && opts->precision != RBO_PREC_MIXED &&
-               opts->precision != RBO_PREC_DF64))
+               opts->precision != RBO_PREC_DF64 && opts->precision != RBO_PREC_OZAKI))
     return RBO_ERR_ARG;
   return RBO_OK;
 }
@@ -370,6 +378,7 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   c.st = st;
   c.mixed = (opts && opts->precision == RBO_PREC_MIXED) ? 1 : 0;
   c.df64 = (opts && opts->precision == RBO_PREC_DF64) ? 1 : 0;
+  c.ozaki = (opts && opts->precision == RBO_PREC_OZAKI) ? 1 : 0;
   c.pip = preproc == RBO_PREPROC_PIP ? 1 : 0;
   if (rand) {
     c.d = sk->d;

@@ -105,6 +105,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   c.st = st;
   c.mixed = (opts && opts->precision == RBO_PREC_MIXED) ? 1 : 0;
   c.df64 = (opts && opts->precision == RBO_PREC_DF64) ? 1 : 0;
+  c.ozaki = (opts && opts->precision == RBO_PREC_OZAKI) ? 1 : 0;
   c.pip = (two && opts && opts->preproc == RBO_PREPROC_PIP) ? 1 : 0;
   // the sketch is only needed by RandCholQR (one-stage) and RandBCGS2 (two-stage)
   const bool sketched = two ? !c.pip : intra == RBO_INTRA_RANDCHOLQR;
@@ -436,7 +437,8 @@ static int sstep_gmres_entry(const rbo_csr* A, const double* Mval, const double*
     code = RBO_ERR_ARG;
   if (code == RBO_OK && !pip && (sk ? sk->d : 4 * (m + 1)) < s_hat) code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->precision != RBO_PREC_FP64 &&
-      opts->precision != RBO_PREC_MIXED && opts->precision != RBO_PREC_DF64)
+      opts->precision != RBO_PREC_MIXED && opts->precision != RBO_PREC_DF64 &&
+      opts->precision != RBO_PREC_OZAKI)
     code = RBO_ERR_ARG;
   if (code == RBO_OK && opts && opts->basis != RBO_BASIS_MONOMIAL && opts->basis != RBO_BASIS_NEWTON &&
       opts->basis != RBO_BASIS_CHEBYSHEV)

@@ -98,6 +98,7 @@ int normalise_column(OrthCtx& c, int64_t n, double* v, double* Rdev, int ldR, in
   const int64_t ldeven = (n + 1) & ~int64_t(1);  // only column 0 is used
   RowPass g;
   g.df64 = c.df64;
+  g.ozaki = c.ozaki;
   g.tag = 13;
   g.n = n;
   g.Y = v;
@@ -116,6 +117,7 @@ int normalise_column(OrthCtx& c, int64_t n, double* v, double* Rdev, int ldR, in
   RBO_TRY(rowpass_launch(g, c.ar, c.st, &c.launches));
   RowPass s;
   s.df64 = c.df64;
+  s.ozaki = c.ozaki;
   s.tag = 13;
   s.n = n;
   s.Y = v;
@@ -133,7 +135,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
   // P1: C1 = Q^T W
   if (p > 0) {
     RowPass r;
-    r.df64 = c.df64; r.tag = 1;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 1;
     r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
     r.acc_x = 1;
     r.mixed = c.mixed;
@@ -143,7 +145,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
   // P2: W = W - Q C1, then sketch -> R_hat (or Gram -> chol for CholQR2)
   {
     RowPass r;
-    r.df64 = c.df64; r.tag = 2;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 2;
     r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
     if (p > 0) { r.C = c.C1; r.write_y = 1; }
     if (rand) {
@@ -159,7 +161,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
   // P3: W = W R_hat^{-1}; R' = chol(W^T W)
   {
     RowPass r;
-    r.df64 = c.df64; r.tag = 3;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 3;
     r.n = n; r.Y = W; r.ldy = ldw; r.b = k;
     r.Tri = c.Rh; r.write_y = 1; r.acc_y = 1;
     r.epi.op = EPI_CHOL; r.epi.out_r = c.Rp; r.epi.block = blk;
@@ -177,7 +179,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
     // P4: W = W R'^{-1}; C2 = Q^T W
     {
       RowPass r;
-      r.df64 = c.df64; r.tag = 4;
+      r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 4;
       r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
       r.Tri = c.Rp; r.write_y = 1; r.acc_x = 1;
       r.epi.op = EPI_STORE; r.epi.out = c.C2; r.epi.out_ld = p;
@@ -186,7 +188,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
     // P5: W = W - Q C2; R2 = chol(W^T W); assemble R
     {
       RowPass r;
-      r.df64 = c.df64; r.tag = 5;
+      r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 5;
       r.n = n; r.X = Q; r.ldx = ldq; r.a = p; r.Y = W; r.ldy = ldw; r.b = k;
       r.C = c.C2; r.write_y = 1; r.acc_y = 1; r.small_coeffs = 1;
       r.epi = fin;
@@ -195,7 +197,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
   } else {
     // no previous basis: W = W R'^{-1} and its Gram in one pass
     RowPass r;
-    r.df64 = c.df64; r.tag = 4;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 4;
     r.n = n; r.Y = W; r.ldy = ldw; r.b = k;
     r.Tri = c.Rp; r.write_y = 1; r.acc_y = 1;
     r.epi = fin;
@@ -203,7 +205,7 @@ int one_stage_block(OrthCtx& c, int64_t n, const double* Q, int64_t ldq, int p, 
   }
   // P6: Q_j = W R2^{-1}
   RowPass r;
-  r.df64 = c.df64; r.tag = 6;
+  r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 6;
   r.n = n; r.Y = W; r.ldy = ldw; r.b = k;
   r.Tri = c.R2; r.write_y = 1;
   return rowpass_launch(r, c.ar, c.st, &c.launches);
@@ -224,7 +226,7 @@ int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
   double* W = bp.VB + (int64_t)cols * bp.ldv;
   if (P > 0) {
     RowPass r;
-    r.df64 = c.df64; r.tag = 7;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 7;
     r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
     r.acc_x = 1;
     r.mixed = c.mixed;
@@ -238,7 +240,7 @@ int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
     // kappa^2 of the accumulation precision.
     if (P > 0) {
       RowPass r;
-      r.df64 = c.df64; r.tag = 8;
+      r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 8;
       r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
       r.C = c.C1 + (size_t)cols * P; r.ldc = P; r.write_y = 1;
       RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
@@ -252,7 +254,7 @@ int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
     RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
   } else {
     RowPass r;
-    r.df64 = c.df64; r.tag = 8;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 8;
     r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = W; r.ldy = bp.ldv; r.b = k;
     if (P > 0) { r.C = c.C1 + (size_t)cols * P; r.ldc = P; r.write_y = 1; }
     set_sketch(r, c);
@@ -263,7 +265,7 @@ int bigpanel_add(OrthCtx& c, BigPanel& bp, int k) {
   }
   {
     RowPass r;
-    r.df64 = c.df64; r.tag = 9;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 9;
     r.n = bp.n; r.X = bp.VB; r.ldx = bp.ldv; r.a = cols; r.Y = W; r.ldy = bp.ldv; r.b = k;
     if (cols > 0) { r.C = c.T + (size_t)cols * K; r.ldc = K; r.acc_x = 1; }
     r.Tri = c.T + cols + (size_t)cols * K; r.ldtri = K;
@@ -292,7 +294,7 @@ int bigpanel_finish(OrthCtx& c, BigPanel& bp, double* Rdev, int ldR, int col0, d
   if (P > 0) {
     {
       RowPass r;
-      r.df64 = c.df64; r.tag = 10;
+      r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 10;
       r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
       r.Tri = c.Rp; r.write_y = 1; r.acc_x = 1;
       r.epi.op = EPI_STORE; r.epi.out = c.C2; r.epi.out_ld = P;
@@ -300,7 +302,7 @@ int bigpanel_finish(OrthCtx& c, BigPanel& bp, double* Rdev, int ldR, int col0, d
     }
     {
       RowPass r;
-      r.df64 = c.df64; r.tag = 11;
+      r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 11;
       r.n = bp.n; r.X = bp.Q; r.ldx = bp.ldq; r.a = P; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
       r.C = c.C2; r.write_y = 1; r.acc_y = 1; r.small_coeffs = 1;
       r.epi = fin;
@@ -308,14 +310,14 @@ int bigpanel_finish(OrthCtx& c, BigPanel& bp, double* Rdev, int ldR, int col0, d
     }
   } else {
     RowPass r;
-    r.df64 = c.df64; r.tag = 10;
+    r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 10;
     r.n = bp.n; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
     r.Tri = c.Rp; r.write_y = 1; r.acc_y = 1;
     r.epi = fin;
     RBO_TRY(rowpass_launch(r, c.ar, c.st, &c.launches));
   }
   RowPass r;
-  r.df64 = c.df64; r.tag = 12;
+  r.df64 = c.df64; r.ozaki = c.ozaki; r.tag = 12;
   r.n = bp.n; r.Y = bp.VB; r.ldy = bp.ldv; r.b = K;
   r.Tri = c.R2; r.write_y = 1;
   return rowpass_launch(r, c.ar, c.st, &c.launches);

@@ -156,11 +156,18 @@ struct RowPass {
                                  // sk_d is then the Count stage, zeta 1)
   int mixed = 0;                 // float32 accumulation of X^T Y' and S Y'
   int df64 = 0;                  // float32-pair arithmetic for the Gram (and small projections)
+  int ozaki = 0;                 // Gram on the tensor cores (exact digit products, ozaki.cu)
+                                 // when the pass shape allows it; float64 otherwise
   int small_coeffs = 0;          // C is a re-orthogonalization (O(eps kappa)) coefficient block
   int max_ctas = 0;              // cap on the grid (0: none); bounds the reduction scratch
   int tag = 0;                   // role for the per-kernel timing (RBO_PROF_PASS_*)
   Epilogue epi;
 };
+
+// Tensor-core Gram pass (ozaki.cu): whether it serves `rp` (rp.ozaki set, a Gram of at most
+// 64 A columns and 8 Y' columns, no projection and no sketch), and its launcher.
+bool ozaki_gram_supported(const RowPass& rp);
+int ozaki_gram_launch(const RowPass& rp, Arena* ar, cudaStream_t st, int* launches, int num_sms);
 
 // Enqueue one row pass; `launches` is incremented per kernel.  Returns RBO_OK or an
 // error for invalid sizes / CUDA launch failures.
@@ -230,6 +237,7 @@ struct OrthCtx {
   int launches = 0;
   int mixed = 0;
   int df64 = 0;   // every pass in float32-pair arithmetic where it applies
+  int ozaki = 0;  // Gram passes on the tensor cores where the pass shape allows
   int d = 0, zeta = 0; uint64_t seed = 0;  // d: rows of the (final) sketch
   int sk_type = 0, d_inner = 0;            // RBO_SKETCH_*; Count-Gauss Count-stage rows
   int pip = 0;      // two-stage preprocessing by BCGS-PIP instead of RandBCGS2

@@ -12,7 +12,7 @@ namespace rbo {
 // the upper triangle is read).  On exit the upper triangle holds R (G = R^T R) and
 // the strict lower triangle is zeroed.  Returns -1, or the first column whose pivot
 // is not positive / not finite (Section 5.1: "non-positive pivots").
-__device__ int cta_cholesky(double* G, int b, int* s_flag) {
+static __device__ int cta_cholesky(double* G, int b, int* s_flag) {
   const int tid = threadIdx.x;
   for (int j = 0; j < b; ++j) {
     if (tid == 0) {
@@ -66,7 +66,7 @@ __device__ inline int tri_rank_deficient(const double* R, int k) {
 // is non-null it receives the thin orthogonal factor (m x k, ld m) with the same
 // column signs.  A is overwritten by the reflectors.  `beta` needs k doubles,
 // `sgn` k doubles, `red` 32 doubles.
-__device__ void cta_householder(double* A, int m, int k, double* R, double* Q, double* beta,
+static __device__ void cta_householder(double* A, int m, int k, double* R, double* Q, double* beta,
                                 double* sgn, double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < k * k; e += blockDim.x) R[e] = 0.0;
@@ -134,7 +134,7 @@ __device__ void cta_householder(double* A, int m, int k, double* R, double* Q, d
 
 // C (p x k, ld p) = Qs^T V for Qs (m x p, ld ldq, global) and V (m x k, ld m, shared):
 // one warp per (i, c) dot product.
-__device__ void cta_gemm_tn(const double* Qs, int ldq, const double* V, int m, int p, int k,
+static __device__ void cta_gemm_tn(const double* Qs, int ldq, const double* V, int m, int p, int k,
                             double* C) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int e = warp; e < p * k; e += nw) {
@@ -150,7 +150,7 @@ __device__ void cta_gemm_tn(const double* Qs, int ldq, const double* V, int m, i
 }
 
 // V (m x k, ld m, shared) -= Qs (m x p, global) C (p x k, ld p)
-__device__ void cta_gemm_nn_sub(const double* Qs, int ldq, const double* C, int m, int p, int k,
+static __device__ void cta_gemm_nn_sub(const double* Qs, int ldq, const double* C, int m, int p, int k,
                                 double* V) {
   for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
     int r = e % m, c = e / m;

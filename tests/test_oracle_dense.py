@@ -1,7 +1,7 @@
 """Pins of the oracle's small dense kernels against library routines and constructions."""
 import numpy as np
 
-from oracle.dense import cholesky_upper, householder_qr, solve_right_upper
+from oracle.dense import cholesky_upper, gram, householder_qr, solve_right_upper
 
 
 def test_cholesky_matches_library():
@@ -58,3 +58,33 @@ def test_solve_right_upper():
     X = solve_right_upper(W, R)
     assert np.allclose(X @ R, W, atol=1e-13)
     assert np.allclose(X, W @ np.linalg.inv(R), atol=1e-12)
+
+
+def test_gram_exact_on_integer_and_dyadic_data():
+    # entries that are small integers times powers of two: every product and partial
+    # sum is exact in float64, so C must equal the integer result exactly; columns of
+    # very different scales and a cancellation (sum 0) included
+    rng = np.random.default_rng(5)
+    X = rng.integers(-1000, 1000, size=(3000, 7)).astype(np.float64)
+    Y = rng.integers(-1000, 1000, size=(3000, 3)).astype(np.float64)
+    X[:, 2] *= 2.0 ** -40
+    Y[:, 1] *= 2.0 ** 30
+    Xi = X.copy()
+    Xi[:, 2] *= 2.0 ** 40
+    Yi = Y.copy()
+    Yi[:, 1] *= 2.0 ** -30
+    exact = (Xi.astype(np.int64).T @ Yi.astype(np.int64)).astype(np.float64)
+    exact[2, :] *= 2.0 ** -40
+    exact[:, 1] *= 2.0 ** 30
+    assert np.array_equal(gram(X, Y), exact)
+    Z = np.vstack([X[:10], -X[:10]])
+    assert np.array_equal(gram(Z, np.vstack([Y[:10], Y[:10]])), np.zeros((7, 3)))
+
+
+def test_gram_is_extended_precision():
+    # x = (1, 2^-60, -1), y = (1, 1, 1): float64 sums left to right give 0; the
+    # extended type (64 significant bits or more) keeps 1 + 2^-60, so the result is
+    # the exact 2^-60
+    X = np.array([[1.0], [2.0 ** -60], [-1.0]])
+    Y = np.ones((3, 1))
+    assert gram(X, Y)[0, 0] == 2.0 ** -60
