@@ -37,6 +37,10 @@
 // A, b <= 8, optionally after the triangular solve y' = y Tri^-1 (float64, written
 // back).  Everything after the per-CTA partials (the fixed-order tree and the small
 // dense epilogue) is shared with the float64 row pass.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -45,20 +49,35 @@
 namespace rbo {
 namespace {
 
-constexpr int OZ_T = 128;            // rows per tile (the exponent chunk)
+constexpr int OZ_T = 128;            // rows per tile
 constexpr int OZ_KS = OZ_T / 16;     // tensor-core K-steps per tile
-constexpr int OZ_NT = 256;           // two warpgroups
+constexpr int OZ_SPLIT = 256;        // splitter threads (two warpgroups)
+constexpr int OZ_NT = OZ_SPLIT + 32; // and one warp issuing the tensor-core products
+constexpr int OZ_RING = 8;           // K-step slots between splitters and the issuing warp
+constexpr int OZ_TRING = 16;         // tile-completion barriers (> OZ_CHUNK)
+constexpr int OZ_CHUNK = 8;          // tiles per accumulation chunk: 1024 rows, so every
+                                     // digit-pair sum stays within 2^24 (exact in float32)
+constexpr int OZ_HEAD = 1;           // a chunk's column scale: its first tile's exponent
+                                     // maximum + OZ_HEAD ...
+constexpr int OZ_WIN = 2;            // ... and later tiles join while their maxima stay
+                                     // within [scale - OZ_WIN, scale]
 constexpr int OZ_MAXA = 64;          // columns of [X Y'] in A
 constexpr int OZ_MAXB = 8;           // columns of Y'
+constexpr int OZ_GSTRIDE = 144;      // bytes per column of a K-step's fixed-point buffer
+                                     // (16 rows of 8 bytes + 16: conflict-free 16-byte reads)
 constexpr uint32_t OZ_TMEM_COLS = 512;
 constexpr unsigned long long OZ_BIAS = 0x0080808080808080ULL;
-static_assert(OZ_NT == NT, "the shared tree reduction strides by NT");
 
 struct OzDev {
+  CUtensorMap tmX;   // X (n x a) and Y (n x b) as 2-D tensors: boxes of OZ_T rows x all
+  CUtensorMap tmY;   // columns, rows past n read as zero
   PassDev P;
   int nA;      // columns of A: a (acc_x) then b (acc_y)
   int N;       // MMA N = 16 ceil(8 b / 16)
-  int off_B;   // B digit tiles: OZ_KS x N rows x 32 bytes
+  int R;       // digits of a column side by side in the lanes: 2 (nA <= 64) or 4 (nA <= 32)
+  int Q;       // A regions (one MMA each) per K-step: ceil(7 / R)
+  int off_B;   // B slots: OZ_RING x N rows x 32 bytes
+  int off_G;   // per warpgroup: fixed points of a K-step, (OZ_MAXA + OZ_MAXB) x OZ_GSTRIDE
 };
 
 // ---- PTX: tensor memory and the tensor-core MMA (tcgen05) ------------------------------
@@ -68,11 +87,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ULL << 46);
 }
-// kind::f16 instruction descriptor: D float32, A and B bf16, both K-major, N >> 3, M >> 4
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// kind::f16 instruction descriptor: D float32, A and B fp16 (format 0), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+// D (tensor memory) [+]= A (tensor memory) B (shared memory descriptor)
+__device__ __forceinline__ void mma_f16(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
@@ -88,6 +109,28 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// one 2-D tile of a tensor map into shared memory (rows x0.., columns 0..), completion
+// counted on `bar`
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x0, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x0), "r"(0), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
 }
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
   asm volatile(
@@ -118,72 +161,160 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---- digits -----------------------------------------------------------------------------
-// Digit I (0 = most significant) of the biased fixed point G as a float (an integer in
-// [-128, 127]): byte 6 - I of G placed in the low byte of 2^23 (0x4B000000), minus
-// 2^23 + 128.
-__device__ __forceinline__ float digit_f(uint32_t glo, uint32_t ghi, int I) {
-  const int k = 6 - I;
-  const uint32_t w = k >= 4 ? ghi : glo;
-  return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(k & 3))) - 8388736.0f;
-}
-// bf16 pair (x: low half, y: high half) of two floats that bf16 represents exactly
-__device__ __forceinline__ uint32_t pack_bf16(float x, float y) {
-  return __byte_perm(__float_as_uint(x), __float_as_uint(y), 0x7632u);
-}
-// F = y 2^(1076 - E) rounded to nearest (ties away from zero), |F| < 2^54 for a value
-// whose exponent field is at most E; zero and subnormal values give 0
+// F = y 2^(1076 - E) rounded to nearest (ties away from zero); |F| < 2^54 for a value
+// whose exponent field is at most E (E >= 1); zero and subnormal values give 0.
 __device__ __forceinline__ long long oz_fix(double y, int E) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(y);
   const int e = (int)((u >> 52) & 0x7FF);
-  if (e == 0) return 0;
   const unsigned long long M = (u & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-  const int sh = e - E + 1;  // <= 1
+  const int k = E - 1 - e;  // right shift; -1 when e == E
   unsigned long long v;
-  if (sh >= 0) {
-    v = M << sh;
-  } else if (sh > -64) {
-    const int k = -sh;
-    v = (M + (1ULL << (k - 1))) >> k;
-  } else {
-    v = 0;
-  }
+  if (k < 0) v = M << 1;
+  else if (k < 63) v = (M + ((1ULL << k) >> 1)) >> k;
+  else v = 0;
+  if (e == 0) v = 0;
   return (u >> 63) ? -(long long)v : (long long)v;
 }
-__device__ __forceinline__ void biased_fix(double v, int E, uint32_t& lo, uint32_t& hi) {
-  const unsigned long long g = (unsigned long long)oz_fix(v, E) + OZ_BIAS;
-  lo = (uint32_t)g;
-  hi = (uint32_t)(g >> 32);
+// the biased fixed point G = F + 0x0080808080808080 as two words
+struct G2 {
+  uint32_t lo, hi;
+};
+// G of y for the column scale exponent E (every value of the column in the chunk has
+// an exponent field <= E): F = round(y 2^(1073 - E)), |F| < 2^51.  Integer operations
+// only: y = +-M 2^(e - 1075) (M the 53-bit significand), so F = +-round(M 2^-(E + 2 - e)),
+// a right shift by k = E + 2 - e >= 2 with the rounding bit added first (ties away
+// from zero).  Zero and subnormal values give F = 0.
+__device__ __forceinline__ unsigned long long int_g(unsigned long long ub, int E) {
+  const int e = (int)((ub >> 52) & 0x7FF);
+  const unsigned long long M = (ub & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const int k = E + 2 - e;
+  unsigned long long r = k < 64 ? (M + (1ULL << (k - 1))) >> k : 0ULL;
+  if (e == 0) r = 0ULL;
+  return (ub >> 63) ? OZ_BIAS - r : OZ_BIAS + r;
 }
-// an exact integer-valued float of magnitude below 2^22 to int
-__device__ __forceinline__ int f2i_exact(float v) {
-  return __float_as_int(v + 12582912.0f) - 0x4B400000;
+__device__ __forceinline__ G2 biased_fix(double v, int E) {
+  const unsigned long long g = (unsigned long long)oz_fix(v, E) + OZ_BIAS;
+  return G2{(uint32_t)g, (uint32_t)(g >> 32)};
+}
+// Digit I = 6 - K of two values (byte K of their G, minus 128) as an fp16 pair: the two
+// bytes placed in the low bytes of the halves of 1024 (0x6400), minus 1152 = 1024 + 128
+// (both exact in fp16); x in the low half.
+template <int K>
+__device__ __forceinline__ uint32_t digit_pair(G2 x, G2 y) {
+  constexpr uint32_t kk = K & 3;
+  constexpr uint32_t sel = kk | (kk << 4) | ((4 + kk) << 8) | ((4 + kk) << 12);
+  const uint32_t t = __byte_perm(K >= 4 ? x.hi : x.lo, K >= 4 ? y.hi : y.lo, sel);
+  const uint32_t u = (t & 0x00FF00FFu) | 0x64006400u;
+  const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&u),
+                            __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// A digits of one column for the 16 rows of a K-step from its fixed points gc (16 x 8
+// bytes): digits I = q R + RHO of region q, row pairs packed, w[8 q + j]
+template <int R, int RHO>
+__device__ __forceinline__ void digits_a(const unsigned char* gc, uint32_t* w) {
+  constexpr int Q = (7 + R - 1) / R;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint4 pr = *reinterpret_cast<const uint4*>(gc + 16 * j);
+    const G2 g0{pr.x, pr.y}, g1{pr.z, pr.w};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int I = q * R + RHO;
+      if (I == 0) w[q * 8 + j] = digit_pair<6>(g0, g1);
+      else if (I == 1) w[q * 8 + j] = digit_pair<5>(g0, g1);
+      else if (I == 2) w[q * 8 + j] = digit_pair<4>(g0, g1);
+      else if (I == 3) w[q * 8 + j] = digit_pair<3>(g0, g1);
+      else if (I == 4) w[q * 8 + j] = digit_pair<2>(g0, g1);
+      else if (I == 5) w[q * 8 + j] = digit_pair<1>(g0, g1);
+      else if (I == 6) w[q * 8 + j] = digit_pair<0>(g0, g1);
+      else w[q * 8 + j] = 0u;
+    }
+  }
+}
+// the same for a byte index k known only at run time (the selector is a register)
+__device__ __forceinline__ uint32_t digit_pair_rt(G2 x, G2 y, int k) {
+  const uint32_t kk = (uint32_t)(k & 3);
+  const uint32_t sel = kk * 0x1111u + 0x4400u;  // bytes kk, kk of x; kk, kk of y
+  const bool h = k >= 4;
+  const uint32_t t = __byte_perm(h ? x.hi : x.lo, h ? y.hi : y.lo, sel);
+  const uint32_t u = (t & 0x00FF00FFu) | 0x64006400u;
+  const __half2 r = __hsub2(*reinterpret_cast<const __half2*>(&u),
+                            __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
+  return *reinterpret_cast<const uint32_t*>(&r);
+}
+// bounded wait (mbarrier.try_wait suspends the thread for a while between polls);
+// false on timeout
+__device__ __forceinline__ bool wait_backoff(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+  return true;
 }
 
 // ---- the kernel ---------------------------------------------------------------------------
+// Roles: warps 0-7 (two warpgroups) split tiles into digits; warpgroup wg produces the
+// K-steps ks = wg, wg + 2, ... of each tile into a ring of OZ_RING slots (A: tensor
+// memory, B: shared memory) and hands each to warp 8, whose lane 0 issues the
+// tensor-core products (mbarriers full / empty per slot).  The accumulators D stay in
+// tensor memory over a chunk of up to OZ_CHUNK tiles that share one scale per column
+// (the first tile's exponent maximum plus OZ_HEAD): a tile whose exponents exceed the
+// chunk's scale, or a full chunk, starts a new chunk after the splitters drained D into
+// 128-bit integer accumulators.
 __global__ void __launch_bounds__(OZ_NT, 1) ozaki_gram_kernel(const __grid_constant__ OzDev D) {
   const PassDev& P = D.P;
   const RowPass& rp = P.p;
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // offsets are taken from a 1024-byte aligned base (the launch adds 1 KB of slack):
+  // tensor copies and the tensor-core operand descriptors need aligned addresses
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ int s_flag;
   __shared__ int s_last;
   __shared__ uint32_t s_tmem;
-  __shared__ int s_E[OZ_MAXA + OZ_MAXB];    // exponent field maximum per column, this tile
+  __shared__ int s_Et[OZ_MAXA + OZ_MAXB];   // exponent field maximum per column, this tile
+  __shared__ int s_Ec[OZ_MAXA + OZ_MAXB];   // column scale exponents of the open chunk
   __shared__ int s_bad[OZ_MAXA + OZ_MAXB];  // a non-finite value met in the column
-  __shared__ __align__(8) uint64_t s_mma_bar;
+  __shared__ int s_exceed, s_abort;
+  __shared__ int s_wgfail[2];
+  __shared__ int s_slot_start[OZ_RING];     // K-step in the slot starts a chunk
+  __shared__ __align__(8) uint64_t s_full[OZ_RING];
+  __shared__ __align__(8) uint64_t s_empty[OZ_RING];
+  __shared__ __align__(8) uint64_t s_tile[OZ_TRING];
+  __shared__ __align__(8) uint64_t s_final;
   if (read_code(P.status) != 0) return;
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wg = warp >> 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool splitter = tid < OZ_SPLIT;
+  const int wg = warp >> 2;  // 0, 1 (2 for the issuing warp)
   const int a = rp.a, b = rp.b, T = OZ_T, TP = P.TP;
-  const int ncol = a + b;     // staged columns: X then Y
-  const int nA = D.nA, N = D.N;
+  const int ncol = a + b;
+  const int nA = D.nA, N = D.N, R = D.R, Q = D.Q;
   const int64_t n = rp.n;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   double* Ts = reinterpret_cast<double*>(smem + P.off_tri);
   double* dinv = reinterpret_cast<double*>(smem + P.off_dinv);
   unsigned char* Bs = smem + D.off_B;
+  auto bar_split = []() { asm volatile("bar.sync 1, 256;" ::: "memory"); };
+  const int wg_bar = 2 + wg;
+  auto bar_wg = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(wg_bar) : "memory"); };
 
   if (rp.Tri) {
     const int ldt = rp.ldtri > 0 ? rp.ldtri : b;
@@ -193,12 +324,22 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozaki_gram_kernel(const __grid_const
     }
     for (int t = tid; t < b; t += OZ_NT) dinv[t] = 1.0 / rp.Tri[t + (size_t)t * ldt];
   }
-  // B tiles: rows 8 yc + 7 and rows >= 8 b stay zero
-  for (int t = tid; t < OZ_KS * N * 8; t += OZ_NT) reinterpret_cast<uint32_t*>(Bs)[t] = 0u;
-  for (int t = tid; t < OZ_MAXA + OZ_MAXB; t += OZ_NT) s_bad[t] = 0;
+  // B slots: rows 8 yc + 7 and rows >= 8 b stay zero
+  for (int t = tid; t < OZ_RING * N * 8; t += OZ_NT) reinterpret_cast<uint32_t*>(Bs)[t] = 0u;
+  for (int t = tid; t < OZ_MAXA + OZ_MAXB; t += OZ_NT) {
+    s_bad[t] = 0;
+    s_Ec[t] = 0;
+  }
   if (tid == 0) {
+    s_abort = 0;
+    s_wgfail[0] = s_wgfail[1] = 0;
     for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
-    mbar_init(&s_mma_bar, 1);
+    for (int s = 0; s < OZ_RING; ++s) {
+      mbar_init(&s_full[s], 4);
+      mbar_init(&s_empty[s], 1);
+    }
+    for (int s = 0; s < OZ_TRING; ++s) mbar_init(&s_tile[s], 1);
+    mbar_init(&s_final, 1);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -210,205 +351,83 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozaki_gram_kernel(const __grid_const
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tA = s_tmem;          // A: K-step ks, region q at columns 32 ks + 8 q
-  const uint32_t tD = s_tmem + 256;    // D_q at columns 256 + q N
-  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-  // this thread's A lane: (parity p, column c)
-  const int L = 32 * (warp & 3) + lane;
-  const int par = L >> 6, xc = L & 63;
-  const bool active = xc < nA;
-
-  // 128-bit integer accumulators: value = acc[yc] * 2^(ea[yc] - 2112)
-  __int128 acc[OZ_MAXB];
-  int ea[OZ_MAXB];
-#pragma unroll
-  for (int c = 0; c < OZ_MAXB; ++c) {
-    acc[c] = 0;
-    ea[c] = -1;
-  }
-
-  auto stage_X = [&](int s) {
-    return reinterpret_cast<double*>(smem + P.off_stage + (size_t)s * P.stage_bytes);
-  };
-  auto issue_tile = [&](int tile, int s) {
-    const int64_t r0 = (int64_t)tile * T;
-    double* xs = stage_X(s);
-    const uint32_t bytes = (uint32_t)T * 8u;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol);
-    __syncwarp();
-    for (int j = lane; j < ncol; j += 32) {
-      const double* src = j < a ? rp.X + j * rp.ldx + r0 : rp.Y + (j - a) * rp.ldy + r0;
-      bulk_copy_g2s(xs + (size_t)j * TP, src, bytes, &bars[s]);
-    }
-  };
-  auto bulk_ok = [&](int tile) { return P.use_bulk && ((int64_t)(tile + 1) * T <= n); };
-
-  uint32_t phase[NST] = {0u, 0u};
-  uint32_t mma_phase = 0u;
-  bool failed = false;
+  const uint32_t tA = s_tmem;                    // A ring: slot s at columns 32 s, region q at + 8 q
+  const uint32_t tD = s_tmem + 32 * OZ_RING;     // D_q at columns 32 OZ_RING + q N
   const int first = blockIdx.x;
-  if (first < P.ntiles && bulk_ok(first) && warp == 0) issue_tile(first, 0);
+  const int ntl = first < P.ntiles ? (P.ntiles - first + (int)gridDim.x - 1) / (int)gridDim.x : 0;
 
-  int it = 0;
-  for (int tile = first; tile < P.ntiles; tile += gridDim.x, ++it) {
-    const int s = it & 1;
-    const int64_t r0 = (int64_t)tile * T;
-    const int rows = (n - r0 < (int64_t)T) ? (int)(n - r0) : T;
-    double* xs = stage_X(s);
-    double* ys = xs + (size_t)a * TP;
-    if (bulk_ok(tile)) {
-      const bool ok = mbar_wait_bounded(&bars[s], phase[s]);
-      phase[s] ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) set_error(P.status, RBO_ERR_TIMEOUT, 11);
-        failed = true;
-        break;
-      }
-    } else {
-      for (int t = tid; t < ncol * T; t += OZ_NT) {
-        const int col = t / T, r = t % T;
-        double v = 0.0;
-        if (r < rows) v = (col < a) ? rp.X[col * rp.ldx + r0 + r] : rp.Y[(col - a) * rp.ldy + r0 + r];
-        xs[(size_t)col * TP + r] = v;
-      }
-      __syncthreads();
-    }
-    const int nxt = tile + gridDim.x;
-    if (warp == 0 && nxt < P.ntiles && bulk_ok(nxt)) {
-      fence_proxy_async();
-      issue_tile(nxt, s ^ 1);
-    }
-
-    // ---- y' = y Tri^-1 (float64), written back --------------------------------------
-    if (rp.Tri) {
-      for (int c0 = 0; c0 < b; c0 += CB) {
-        const int cw = min(CB, b - c0);
-        if (c0 > 0) {
-          for (int t = tid; t < T * cw; t += OZ_NT) {
-            const int r = t % T, c = c0 + t / T;
-            double v = ys[c * TP + r];
-            for (int i = 0; i < c0; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
-            ys[c * TP + r] = v;
+  // ======================= tensor-core issue (warp 8, lane 0) =============================
+  if (!splitter) {
+    if (lane == 0) {
+      const uint32_t id = idesc_f16(128, N);
+      bool ok = true;
+      for (int it = 0; it < ntl && ok; ++it) {
+        for (int ks = 0; ks < OZ_KS; ++ks) {
+          const int g = it * OZ_KS + ks, slot = g % OZ_RING;
+          if (!wait_backoff(&s_full[slot], (uint32_t)((g / OZ_RING) & 1))) {
+            set_error(P.status, RBO_ERR_TIMEOUT, 13);
+            ok = false;
+            break;
           }
-          __syncthreads();
+          tc_fence_after();
+          const uint32_t acc = s_slot_start[slot] ? 0u : 1u;
+          const uint64_t db = smem_desc(smem_u32(Bs + (size_t)slot * N * 32), 128, 256);
+          for (int q = 0; q < Q; ++q)
+            mma_f16(tD + (uint32_t)(q * N), tA + (uint32_t)(32 * slot + 8 * q), db, id, acc);
+          mma_commit(&s_empty[slot]);
         }
-        for (int r = tid; r < T; r += OZ_NT) {
-          for (int c = c0; c < c0 + cw; ++c) {
-            double v = ys[c * TP + r];
-            for (int i = c0; i < c; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
-            ys[c * TP + r] = v * dinv[c];
-          }
-        }
-        __syncthreads();
+        if (ok) mma_commit(&s_tile[it % OZ_TRING]);
       }
-      if (rp.write_y)
-        for (int t = tid; t < b * T; t += OZ_NT) {
-          const int c = t / T, rr = t % T;
-          if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = ys[(size_t)c * TP + rr];
-        }
+      // every product issued has completed before the tensor memory is freed
+      mma_commit(&s_final);
+      mbar_wait_bounded(&s_final, 0u);
     }
-
-    // ---- exponent field maxima of the tile's columns ----------------------------------
-    for (int c = tid; c < ncol; c += OZ_NT) s_E[c] = 0;
-    __syncthreads();
-    for (int t = tid; t < ncol * T; t += OZ_NT) {
-      const int c = t / T, r = t % T;   // T a multiple of 32: a warp shares one column
-      const uint32_t hi = (uint32_t)__double2hiint(xs[(size_t)c * TP + r]);
-      int ex = (int)((hi >> 20) & 0x7FFu);
-      ex = __reduce_max_sync(0xffffffffu, ex);
-      if (lane == 0 && ex != 0) atomicMax(&s_E[c], ex);
+  } else {
+    // ======================= splitters (warps 0-7) =========================================
+    const int wq = warp & 3;
+    const int L = 32 * wq + lane;                 // this thread's A lane
+    const int rho = R == 2 ? (wq >> 1) : wq;      // digit group (warp-uniform)
+    const int xc = R == 2 ? (L & 63) : lane;      // A column
+    const bool active = xc < nA;
+    const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
+    __int128 acc[OZ_MAXB];
+    int ea[OZ_MAXB];
+#pragma unroll
+    for (int c = 0; c < OZ_MAXB; ++c) {
+      acc[c] = 0;
+      ea[c] = -1;
     }
-    __syncthreads();
-    for (int c = tid; c < ncol; c += OZ_NT)
-      if (s_E[c] == 0x7FF) s_bad[c] = 1;
-
-    // ---- digits: A into tensor memory, B into shared memory ----------------------------
-    for (int ks = wg; ks < OZ_KS; ks += 2) {
-      uint32_t w[32];
-      if (active) {
-        const double* col = xs + (size_t)xc * TP + ks * 16;
-        const int E = s_E[xc];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const double2 v = *reinterpret_cast<const double2*>(col + 2 * j);
-          uint32_t g0l, g0h, g1l, g1h;
-          biased_fix(v.x, E, g0l, g0h);
-          biased_fix(v.y, E, g1l, g1h);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int I = 2 * q + par;
-            w[q * 8 + j] = I <= 6 ? pack_bf16(digit_f(g0l, g0h, I), digit_f(g1l, g1h, I)) : 0u;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) w[j] = 0u;
-      }
-      tmem_st32(tA + (uint32_t)(32 * ks) + lane_base, w);
-      // B: Y' digits of the K-step's 16 rows, row 8 yc + J of the K-major tile
-      unsigned char* Bk = Bs + (size_t)ks * N * 32;
-      for (int e = tid & 127; e < 16 * b; e += 128) {
-        const int r = e & 15, yc = e >> 4;
-        uint32_t gl, gh;
-        biased_fix(ys[(size_t)yc * TP + ks * 16 + r], s_E[a + yc], gl, gh);
-#pragma unroll
-        for (int J = 0; J < 7; ++J) {
-          const int nrow = 8 * yc + J;
-          const uint32_t bits = __float_as_uint(digit_f(gl, gh, J)) >> 16;
-          *reinterpret_cast<uint16_t*>(Bk + (nrow >> 3) * 256 + (r >> 3) * 128 + (nrow & 7) * 16 +
-                                       (r & 7) * 2) = (uint16_t)bits;
-        }
-      }
-    }
-    tmem_wait_st();
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-
-    // ---- tensor-core products of the tile ------------------------------------------------
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t id = idesc_bf16(128, N);
-      for (int ks = 0; ks < OZ_KS; ++ks) {
-        const uint64_t db = smem_desc(smem_u32(Bs + (size_t)ks * N * 32), 128, 256);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          mma_ts(tD + (uint32_t)(q * N), tA + (uint32_t)(32 * ks + 8 * q), db, id, ks > 0 ? 1u : 0u);
-      }
-      mma_commit(&s_mma_bar);
-    }
-    __syncwarp();
-    const bool done = mbar_wait_bounded(&s_mma_bar, mma_phase);
-    mma_phase ^= 1u;
-    tc_fence_after();
-    if (__syncthreads_or(!done)) {
-      if (tid == 0) set_error(P.status, RBO_ERR_TIMEOUT, 12);
-      mbar_wait_bounded(&s_mma_bar, mma_phase ^ 1u);  // a second bounded chance before freeing
-      failed = true;
-      break;
-    }
-
-    // ---- drain: warpgroup wg reads the regions q = 2 wg, 2 wg + 1 ------------------------
-    {
+    auto stage_X = [&](int s) {
+      return reinterpret_cast<double*>(smem + P.off_stage + (size_t)s * P.stage_bytes);
+    };
+    // a tile: two tensor copies (X box, Y box) issued by one thread
+    auto issue_tile = [&](int tile, int s) {
+      if (lane != 0) return;
+      const int r0 = tile * T;
+      double* xs = stage_X(s);
+      mbar_arrive_expect_tx(&bars[s], (uint32_t)T * 8u * (uint32_t)ncol);
+      if (a > 0) tma_load_2d(xs, &D.tmX, r0, &bars[s]);
+      tma_load_2d(xs + (size_t)a * TP, &D.tmY, r0, &bars[s]);
+    };
+    // drain D (all products of the open chunk complete) into the 128-bit accumulators
+    auto drain = [&]() {
       long long hi[OZ_MAXB], lo[OZ_MAXB];
 #pragma unroll
       for (int c = 0; c < OZ_MAXB; ++c) { hi[c] = 0; lo[c] = 0; }
+      const int q0 = wg * (Q / 2), q1 = q0 + Q / 2;
+      for (int q = q0; q < q1; ++q) {
+        const int I = q * R + rho;
 #pragma unroll
-      for (int qq = 0; qq < 2; ++qq) {
-        const int q = 2 * wg + qq;
-        const int I = 2 * q + par;
-        float v[64];
-        tmem_ld32(tD + (uint32_t)(q * N) + lane_base, v);
-        tmem_ld32(tD + (uint32_t)(q * N + 32) + lane_base, v + 32);
-        if (active && I <= 6) {
-#pragma unroll
-          for (int yc = 0; yc < OZ_MAXB; ++yc) {
-            if (yc < b) {
+        for (int yc = 0; yc < OZ_MAXB; ++yc) {
+          if (yc < b) {  // b is uniform: the loads stay warp-converged
+            float v[8];
+            tmem_ld8(tD + (uint32_t)(q * N + 8 * yc) + lane_base, v);
+            if (active && I <= 6) {
 #pragma unroll
               for (int J = 0; J < 7; ++J) {
                 const int Lv = I + J;
                 if (Lv <= 7) {
-                  const long long iv = (long long)f2i_exact(v[8 * yc + J]);
+                  const long long iv = (long long)__float2int_rn(v[J]);
                   if (Lv <= 3) hi[yc] += iv << (8 * (3 - Lv));
                   else lo[yc] += iv << (8 * (7 - Lv));
                 }
@@ -423,15 +442,15 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozaki_gram_kernel(const __grid_const
           if (yc < b) {
             const __int128 S = ((__int128)hi[yc] << 32) + (__int128)lo[yc];
             if (S != 0) {
-              const int Tt = s_E[xc] + s_E[a + yc];
+              const int Tt = s_Ec[xc] + s_Ec[a + yc];
               if (ea[yc] < 0) ea[yc] = Tt;
               int sh = Tt - ea[yc];
-              // |S| < 2^80; a shift of at most 24 keeps the sum of the CTA's tiles far
+              // |S| < 2^83; a shift of at most 20 keeps the sum of the CTA's chunks far
               // below 2^127
-              if (sh > 24) {  // magnitude grew: renormalise the accumulator
-                acc[yc] >>= (sh - 24);
-                ea[yc] += sh - 24;
-                sh = 24;
+              if (sh > 20) {
+                acc[yc] >>= (sh - 20);
+                ea[yc] += sh - 20;
+                sh = 20;
               }
               if (sh >= 0) acc[yc] += S << sh;
               else if (sh > -120) acc[yc] += S >> (-sh);
@@ -439,36 +458,255 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozaki_gram_kernel(const __grid_const
           }
         }
       }
+    };
+
+    uint32_t phase[NST] = {0u, 0u};
+    bool chunk_open = false;
+    int tiles_in_chunk = 0;
+    if (ntl > 0 && warp == 0) issue_tile(first, 0);
+    int it = 0;
+    for (; it < ntl; ++it) {
+      const int tile = first + it * (int)gridDim.x;
+      const int s = it & 1;
+      const int64_t r0 = (int64_t)tile * T;
+      const int rows = (n - r0 < (int64_t)T) ? (int)(n - r0) : T;
+      double* xs = stage_X(s);
+      double* ys = xs + (size_t)a * TP;
+      if (tid == 0) s_exceed = 0;
+      {
+        const bool ok = wait_backoff(&bars[s], phase[s]);
+        if (!__all_sync(0xffffffffu, ok) && lane == 0) {
+          set_error(P.status, RBO_ERR_TIMEOUT, 11);
+          s_abort = 1;
+        }
+        phase[s] ^= 1u;
+      }
+      bar_split();
+      if (s_abort) break;
+      if (it + 1 < ntl && warp == 0) {
+        fence_proxy_async();
+        issue_tile(tile + (int)gridDim.x, s ^ 1);
+      }
+
+      // ---- y' = y Tri^-1 (float64), written back ----------------------------------------
+      if (rp.Tri) {
+        for (int c0 = 0; c0 < b; c0 += CB) {
+          const int cw = min(CB, b - c0);
+          if (c0 > 0) {
+            for (int t = tid; t < T * cw; t += OZ_SPLIT) {
+              const int r = t % T, c = c0 + t / T;
+              double v = ys[c * TP + r];
+              for (int i = 0; i < c0; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
+              ys[c * TP + r] = v;
+            }
+            bar_split();
+          }
+          for (int r = tid; r < T; r += OZ_SPLIT) {
+            for (int c = c0; c < c0 + cw; ++c) {
+              double v = ys[c * TP + r];
+              for (int i = c0; i < c; ++i) v = fma(-ys[i * TP + r], Ts[i + c * b], v);
+              ys[c * TP + r] = v * dinv[c];
+            }
+          }
+          bar_split();
+        }
+        if (rp.write_y)
+          for (int t = tid; t < b * T; t += OZ_SPLIT) {
+            const int c = t / T, rr = t % T;
+            if (rr < rows) rp.Y[c * rp.ldy + r0 + rr] = ys[(size_t)c * TP + rr];
+          }
+        fence_proxy_async();  // the stage was written here; a later tensor copy reuses it
+      }
+
+      // ---- exponent field maxima; a new chunk when they exceed the chunk's scales -------
+      // one warp per column (columns warp, warp + 8, ...): every load first, four rows
+      // per lane and column, then the warp maxima
+      {
+        constexpr int NCW = (OZ_MAXA + OZ_MAXB) / (OZ_SPLIT / 32);
+        uint32_t m[NCW];
+#pragma unroll
+        for (int i = 0; i < NCW; ++i) {
+          const int c = warp + 8 * i;
+          m[i] = 0u;
+          if (c < ncol) {
+            const uint32_t* col = reinterpret_cast<const uint32_t*>(xs + (size_t)c * TP);
+#pragma unroll
+            for (int k = 0; k < T / 32; ++k) m[i] = max(m[i], col[2 * (32 * k + lane) + 1] & 0x7FFFFFFFu);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NCW; ++i) {
+          const int c = warp + 8 * i;
+          const uint32_t e = __reduce_max_sync(0xffffffffu, (m[i] >> 20) & 0x7FFu);
+          if (lane == 0 && c < ncol) s_Et[c] = (int)e;
+        }
+      }
+      bar_split();
+      for (int c = tid; c < ncol; c += OZ_SPLIT) {
+        // outside the chunk's window: larger values would overflow its fixed point,
+        // much smaller ones would lose bits (a column of zeros fits every window)
+        if (s_Et[c] > s_Ec[c] || (s_Et[c] != 0 && s_Et[c] < s_Ec[c] - OZ_WIN)) s_exceed = 1;
+        if (s_Et[c] == 0x7FF) s_bad[c] = 1;
+      }
+      bar_split();
+      const bool new_chunk = !chunk_open || tiles_in_chunk == OZ_CHUNK || s_exceed;
+      if (new_chunk) {
+        if (chunk_open) {
+          const int pt = it - 1;
+          const bool ok = wait_backoff(&s_tile[pt % OZ_TRING], (uint32_t)((pt / OZ_TRING) & 1));
+          if (!__all_sync(0xffffffffu, ok) && lane == 0) {
+            set_error(P.status, RBO_ERR_TIMEOUT, 14);
+            s_abort = 1;
+          }
+          bar_split();
+          if (s_abort) break;
+          tc_fence_after();
+          drain();
+          tc_fence_before();
+        }
+        bar_split();
+        for (int c = tid; c < ncol; c += OZ_SPLIT) s_Ec[c] = s_Et[c] + OZ_HEAD;
+        bar_split();
+        chunk_open = true;
+        tiles_in_chunk = 0;
+      }
+      ++tiles_in_chunk;
+
+      // ---- digits of this warpgroup's K-steps: A into tensor memory, B into shared ------
+      // Per K-step: (1) the 128 threads of the warpgroup form the biased fixed point of
+      // every value of the 16 rows (each value once) in the warpgroup's buffer; (2) each
+      // A lane reads its column's 16 values and packs its digits; the B tasks pack the
+      // Y' digits.
+      bool fail = false;
+      const int t128 = tid & 127;
+      unsigned char* gb = smem + D.off_G + (size_t)wg * (OZ_MAXA + OZ_MAXB) * OZ_GSTRIDE;
+      for (int ks = wg; ks < OZ_KS; ks += 2) {
+        const int g = it * OZ_KS + ks, slot = g % OZ_RING;
+        {
+          const int r = t128 & 15;
+          const int c0 = t128 >> 4;
+          constexpr int NCI = (OZ_MAXA + OZ_MAXB) / 8;
+          unsigned long long u[NCI];
+          int E[NCI];
+#pragma unroll
+          for (int i = 0; i < NCI; ++i) {  // every load first
+            const int c = c0 + 8 * i;
+            u[i] = c < ncol ? (unsigned long long)__double_as_longlong(xs[(size_t)c * TP + ks * 16 + r]) : 0ULL;
+            E[i] = c < ncol ? s_Ec[c] : 0;
+          }
+#pragma unroll
+          for (int i = 0; i < NCI; ++i) {
+            const int c = c0 + 8 * i;
+            if (c < ncol)
+              *reinterpret_cast<unsigned long long*>(gb + (size_t)c * OZ_GSTRIDE + r * 8) = int_g(u[i], E[i]);
+          }
+        }
+        // the slot's previous products have completed (its A and B may be overwritten)
+        const bool ok = g < OZ_RING || wait_backoff(&s_empty[slot], (uint32_t)(((g / OZ_RING) - 1) & 1));
+        if (!ok) {
+          set_error(P.status, RBO_ERR_TIMEOUT, 15);
+          s_wgfail[wg] = 1;
+        }
+        bar_wg();
+        if (s_wgfail[wg]) {  // uniform in the warpgroup
+          fail = true;
+          break;
+        }
+        tc_fence_after();
+        uint32_t w[32];
+#pragma unroll
+        for (int j2 = 0; j2 < 32; ++j2) w[j2] = 0u;
+        if (active) {
+          const unsigned char* gc = gb + (size_t)xc * OZ_GSTRIDE;
+          if (R == 2) {
+            if (rho == 0) digits_a<2, 0>(gc, w);
+            else digits_a<2, 1>(gc, w);
+          } else {
+            switch (rho) {
+              case 0: digits_a<4, 0>(gc, w); break;
+              case 1: digits_a<4, 1>(gc, w); break;
+              case 2: digits_a<4, 2>(gc, w); break;
+              default: digits_a<4, 3>(gc, w); break;
+            }
+          }
+        }
+        if (R == 2) tmem_st32(tA + (uint32_t)(32 * slot) + lane_base, w);
+        else tmem_st16(tA + (uint32_t)(32 * slot) + lane_base, w);
+        // B: Y' digits, row 8 yc + J of the K-major slot, one digit pair per task
+        unsigned char* Bk = Bs + (size_t)slot * N * 32;
+        if (t128 < 8 * b) {
+          const int jp = t128 & 7, yc = t128 >> 3;
+          const uint4 pr = *reinterpret_cast<const uint4*>(gb + (size_t)(a + yc) * OZ_GSTRIDE + 16 * jp);
+          const G2 g0{pr.x, pr.y}, g1{pr.z, pr.w};
+          uint32_t* dst = reinterpret_cast<uint32_t*>(Bk + yc * 256 + (jp >> 2) * 128 + (jp & 3) * 4);
+          dst[0] = digit_pair<6>(g0, g1);   // rows 8 yc + J are 16 bytes apart
+          dst[4] = digit_pair<5>(g0, g1);
+          dst[8] = digit_pair<4>(g0, g1);
+          dst[12] = digit_pair<3>(g0, g1);
+          dst[16] = digit_pair<2>(g0, g1);
+          dst[20] = digit_pair<1>(g0, g1);
+          dst[24] = digit_pair<0>(g0, g1);
+        }
+        if (t128 == 0) s_slot_start[slot] = (new_chunk && ks == 0) ? 1 : 0;
+        tmem_wait_st();
+        if (t128 < 8 * b) fence_proxy_async();  // B written through the generic proxy
+        tc_fence_before();
+        bar_wg();  // the buffer is free for the next K-step; the slot is complete
+        if (lane == 0) mbar_arrive(&s_full[slot]);
+      }
+      if (fail) s_abort = 1;
+      bar_split();  // stage s free; every K-step of the tile handed over
+      if (s_abort) break;
     }
-    tc_fence_before();
-    __syncthreads();  // D, A, B and stage s free for the next tile
+    // ---- the last chunk ------------------------------------------------------------------
+    if (!s_abort && chunk_open && it == ntl) {
+      const int pt = ntl - 1;
+      const bool ok = wait_backoff(&s_tile[pt % OZ_TRING], (uint32_t)((pt / OZ_TRING) & 1));
+      if (!__all_sync(0xffffffffu, ok) && lane == 0) {
+        set_error(P.status, RBO_ERR_TIMEOUT, 14);
+        s_abort = 1;
+      }
+      bar_split();
+      if (!s_abort) {
+        tc_fence_after();
+        drain();
+      }
+    }
+    bar_split();
+    // per-CTA partial contributions: (warpgroup, digit group) slot of every output
+    double* comb = reinterpret_cast<double*>(smem + P.off_stage);  // 8 x 64 x 8
+    const int cslot = wg * 4 + rho;
+    if (!s_abort)
+      for (int t = tid; t < 8 * OZ_MAXA * OZ_MAXB; t += OZ_SPLIT) comb[t] = 0.0;
+    bar_split();
+    if (!s_abort && active) {
+#pragma unroll
+      for (int yc = 0; yc < OZ_MAXB; ++yc) {
+        if (yc < b && ea[yc] >= 0)
+          comb[((size_t)cslot * OZ_MAXA + xc) * OZ_MAXB + yc] = ldexp((double)acc[yc], ea[yc] - 2106);
+      }
+    }
   }
 
-  // ---- free the tensor memory ---------------------------------------------------------------
+  // ---- free the tensor memory (every issued product has completed) -------------------------
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && read_code(P.status) != 0) s_abort = 1;
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem),
                  "r"(OZ_TMEM_COLS));
   }
-  if (failed || P.L == 0) return;
-
-  // ---- per-CTA partial: four threads hold parts of every output ----------------------------
-  double* comb = reinterpret_cast<double*>(smem + P.off_stage);  // 4 x 64 x 8
-#pragma unroll
-  for (int yc = 0; yc < OZ_MAXB; ++yc) {
-    double v = 0.0;
-    if (ea[yc] >= 0) v = ldexp((double)acc[yc], ea[yc] - 2112);
-    comb[((size_t)(wg * 2 + par) * OZ_MAXA + xc) * OZ_MAXB + yc] = v;
-  }
   __syncthreads();
+  if (s_abort || P.L == 0) return;
+
+  const double* comb = reinterpret_cast<const double*>(smem + P.off_stage);
   double* mypart = P.partials + (size_t)blockIdx.x * P.L;
   for (int o = tid; o < P.no; o += OZ_NT) {
     const int i = o / b, c = o % b;
     double sum = 0.0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) sum += comb[((size_t)k * OZ_MAXA + i) * OZ_MAXB + c];
+    for (int k = 0; k < 8; ++k) sum += comb[((size_t)k * OZ_MAXA + i) * OZ_MAXB + c];
     if (s_bad[i] || s_bad[a + c]) sum = __longlong_as_double(0x7FF8000000000000LL);
     mypart[o] = sum;
   }
@@ -480,11 +718,43 @@ int g_oz_smem_set[64] = {};
 
 }  // namespace
 
+// 2-D tensor map of a column-major float64 array (n rows, cols columns, leading
+// dimension ld): boxes of OZ_T rows x cols columns, out-of-range rows read as zero.
+static int make_tensor_map(CUtensorMap* m, const double* base, int64_t n, int cols, int64_t ld) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_oz_mu);
+    if (encode == nullptr) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+              cudaSuccess ||
+          q != cudaDriverEntryPointSuccess || fn == nullptr) {
+        cudaGetLastError();
+        return RBO_ERR_CUDA;
+      }
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)OZ_T, (cuuint32_t)cols};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(base), dims,
+                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RBO_OK : RBO_ERR_CUDA;
+}
+
 bool ozaki_gram_supported(const RowPass& rp) {
   if (!rp.ozaki || rp.C || rp.sk_d > 0 || rp.sk_gd > 0 || rp.mixed || rp.df64) return false;
   if (!rp.acc_x && !rp.acc_y) return false;
   if (rp.b < 1 || rp.b > OZ_MAXB) return false;
   const int a = rp.acc_x ? rp.a : 0;
+  // tensor copies: 16-byte aligned bases and column strides, row coordinates in int
+  if (rp.n >= (int64_t)1 << 31) return false;
+  if (((uintptr_t)rp.Y & 15) != 0 || (rp.ldy % 2) != 0) return false;
+  if (a > 0 && (((uintptr_t)rp.X & 15) != 0 || (rp.ldx % 2) != 0)) return false;
   const int nA = a + (rp.acc_y ? rp.b : 0);
   return nA >= 1 && nA <= OZ_MAXA;
 }
@@ -497,9 +767,9 @@ int ozaki_gram_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* laun
   const int nA = a + (rp.acc_y ? b : 0);
   const int N = ((8 * b + 15) / 16) * 16;
   const int zr = nA, no = zr * b, L = no;
-  const int TP = OZ_T + 2;
+  const int TP = OZ_T;  // the tensor copies fill columns of exactly OZ_T rows
   const size_t stage_bytes = (size_t)(a + b) * TP * 8;
-  size_t o = 64;
+  size_t o = 1024;       // tensor-copy destinations 128-byte aligned
   const size_t off_stage = o;
   o += NST * stage_bytes;
   const size_t off_tri = o;
@@ -508,11 +778,14 @@ int ozaki_gram_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* laun
   o += (size_t)b * 8;
   o = (o + 1023) & ~size_t(1023);
   const size_t off_B = o;
-  o += (size_t)OZ_KS * N * 32;
+  o += (size_t)OZ_RING * N * 32;
+  const size_t off_G = o;
+  o += (size_t)2 * (OZ_MAXA + OZ_MAXB) * OZ_GSTRIDE;
   size_t epi = 64 + ((size_t)L + 2) * 8 + (size_t)b * b * 2 * 8 + 64 * 8;
-  size_t comb = off_stage + (size_t)4 * OZ_MAXA * OZ_MAXB * 8;
+  size_t comb = off_stage + (size_t)8 * OZ_MAXA * OZ_MAXB * 8;
   // at least 116 KB: one CTA per SM (each holds all 512 tensor-memory columns)
   size_t smem = std::max(std::max(o, epi), std::max(comb, (size_t)116 * 1024));
+  smem += 1024;  // alignment slack of the kernel's base
   if (smem > 220 * 1024) return RBO_ERR_ARG;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -536,9 +809,7 @@ int ozaki_gram_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* laun
   P.T = OZ_T;
   P.TP = TP;
   P.ntiles = ntiles;
-  const bool alignedX = a == 0 || (((uintptr_t)rp.X & 15) == 0 && (rp.ldx % 2) == 0);
-  const bool alignedY = (((uintptr_t)rp.Y & 15) == 0 && (rp.ldy % 2) == 0);
-  P.use_bulk = (alignedX && alignedY) ? 1 : 0;
+  P.use_bulk = 1;
   P.zr = zr;
   P.no = no;
   P.L = L;
@@ -557,7 +828,15 @@ int ozaki_gram_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* laun
   P.tickets = ar->tickets;
   D.nA = nA;
   D.N = N;
+  D.R = nA <= 32 ? 4 : 2;
+  D.Q = (7 + D.R - 1) / D.R;
   D.off_B = (int)off_B;
+  D.off_G = (int)off_G;
+  {
+    int e = make_tensor_map(&D.tmY, rp.Y, rp.n, b, rp.ldy);
+    if (e == RBO_OK && a > 0) e = make_tensor_map(&D.tmX, rp.X, rp.n, a, rp.ldx);
+    if (e != RBO_OK) return e;
+  }
   ProfToken tok = prof_start(st);
   ozaki_gram_kernel<<<G, OZ_NT, smem, st>>>(D);
   if (prof_on()) {

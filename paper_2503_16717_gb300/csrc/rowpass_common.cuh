@@ -338,7 +338,7 @@ __device__ __forceinline__ void tree_reduce_epilogue(const PassDev& P, unsigned 
   {
     const double* base = P.partials + (size_t)g * GROUP * P.L;
     double* gout = P.gpart + (size_t)g * P.L;
-    for (int t = tid; t < P.L; t += NT) {
+    for (int t = tid; t < P.L; t += (int)blockDim.x) {
       double s = 0.0;
       double v[GROUP];
 #pragma unroll
@@ -360,7 +360,7 @@ __device__ __forceinline__ void tree_reduce_epilogue(const PassDev& P, unsigned 
   if (!s_last) return;
   __threadfence();
   double* red = reinterpret_cast<double*>(smem + P.off_red);
-  for (int t = tid; t < P.L; t += NT) {
+  for (int t = tid; t < P.L; t += (int)blockDim.x) {
     double s = 0.0;
     for (int i0 = 0; i0 < P.ngroups; i0 += 8) {
       double v[8];

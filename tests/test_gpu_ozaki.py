@@ -3,10 +3,12 @@ digits on the bf16 tensor cores) against the oracle, and of the orthogonalizatio
 schemes and s-step GMRES in that mode against the float64 tolerances.
 
 Error bound of the digit Gram, per row and tile of 128 rows (Mx, My: the largest
-magnitudes of the two columns in the tile): each value is rounded to a multiple of
-2^-53 Mx (2^-53 My), an error of at most 2^-54 Mx, and the dropped digit pairs
-(levels 8..12) weigh at most 5 * 2^14 * 2^32 / 2^106 < 2^-57 of Mx My, so
-|C - X^T Y|_ij <= 2^-51 sum_t 128 Mx My over the tiles t."""
+magnitudes of the two columns in the tile): a tile shares its column's fixed-point
+scale with the other tiles of its accumulation chunk only while its exponent maximum
+stays within two of the scale's, so every value is rounded to a multiple of at most
+2^-48 Mx (an error of at most 2^-49 Mx), and the dropped digit pairs (levels 8..12)
+weigh at most 5 * 2^14 * 2^32 / 2^98 < 2^-49 of Mx My, so
+|C - X^T Y|_ij <= 2^-47 sum_t 128 Mx My over the tiles t."""
 import numpy as np
 import pytest
 
@@ -34,7 +36,7 @@ def _bound(X, Y):
     pad = nt * TILE - n
     Xa = np.abs(np.vstack([X, np.zeros((pad, X.shape[1]))])).reshape(nt, TILE, -1).max(axis=1)
     Ya = np.abs(np.vstack([Y, np.zeros((pad, Y.shape[1]))])).reshape(nt, TILE, -1).max(axis=1)
-    return 2.0 ** -51 * TILE * (Xa.T @ Ya)
+    return 2.0 ** -47 * TILE * (Xa.T @ Ya)
 
 
 def _scaled(rng, n, k, scales):
