@@ -303,7 +303,7 @@ int rbo_gram_ex(int64_t n, int32_t a, const double* X, int64_t ldx, int32_t b, c
   RowPass r;
   r.n = n; r.X = X; r.ldx = ldx; r.a = a; r.Y = const_cast<double*>(Y); r.ldy = ldy; r.b = b;
   r.acc_x = 1;
-  r.ozaki = precision == RBO_PREC_OZAKI ? 1 : 0;
+  r.ozaki = precision == RBO_PREC_OZAKI ? 2 : 0;  // the caller asked for this kernel
   r.epi.op = EPI_STORE; r.epi.out = dout; r.epi.out_ld = a;
   int launches = 0;
   if ((e = rowpass_launch(r, ar, st, &launches))) return e;

@@ -156,8 +156,9 @@ struct RowPass {
                                  // sk_d is then the Count stage, zeta 1)
   int mixed = 0;                 // float32 accumulation of X^T Y' and S Y'
   int df64 = 0;                  // float32-pair arithmetic for the Gram (and small projections)
-  int ozaki = 0;                 // Gram on the tensor cores (exact digit products, ozaki.cu)
-                                 // when the pass shape allows it; float64 otherwise
+  int ozaki = 0;                 // Gram on the tensor cores (exact digit products, ozaki.cu):
+                                 // 1 where the pass shape allows it and it is the faster
+                                 // kernel, 2 wherever the shape allows it; float64 otherwise
   int small_coeffs = 0;          // C is a re-orthogonalization (O(eps kappa)) coefficient block
   int max_ctas = 0;              // cap on the grid (0: none); bounds the reduction scratch
   int tag = 0;                   // role for the per-kernel timing (RBO_PROF_PASS_*)
@@ -167,6 +168,10 @@ struct RowPass {
 // Tensor-core Gram pass (ozaki.cu): whether it serves `rp` (rp.ozaki set, a Gram of at most
 // 64 A columns and 8 Y' columns, no projection and no sketch), and its launcher.
 bool ozaki_gram_supported(const RowPass& rp);
+// Whether the digit-product kernel beats the float64 pass for this shape: its time per
+// row is nearly flat in the column count (the digit formation and the tensor-core
+// handshakes per 16-row step dominate), the float64 pass's grows with a * b.
+bool ozaki_gram_pays(const RowPass& rp);
 int ozaki_gram_launch(const RowPass& rp, Arena* ar, cudaStream_t st, int* launches, int num_sms);
 
 // Enqueue one row pass; `launches` is incremented per kernel.  Returns RBO_OK or an

@@ -647,8 +647,10 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   if (rp.a > 0 && rp.X == nullptr) return RBO_ERR_ARG;
   if (rp.a == 0) { rp.C = nullptr; rp.acc_x = 0; }
   // Gram passes of the tensor-core mode go to the digit-product kernel when their shape
-  // allows it (ozaki.cu); every other pass runs here in float64
-  if (rp.ozaki && ozaki_gram_supported(rp)) return ozaki_gram_launch(rp, ar, st, launches, sm_count());
+  // allows it and (unless the caller asked for it outright, ozaki == 2) when it beats
+  // the float64 pass (ozaki.cu); every other pass runs here in float64
+  if (rp.ozaki && ozaki_gram_supported(rp) && (rp.ozaki == 2 || ozaki_gram_pays(rp)))
+    return ozaki_gram_launch(rp, ar, st, launches, sm_count());
   if (rp.sk_d > DMAX || rp.sk_zeta > ZMAX) return RBO_ERR_ARG;
   if (rp.sk_gd < 0 || rp.sk_gd > 256 || rp.sk_cg < 0 || rp.sk_cg > DMAX) return RBO_ERR_ARG;
   if (rp.sk_gd > 0 && rp.sk_d > 0) return RBO_ERR_ARG;

@@ -5,10 +5,10 @@ schemes and s-step GMRES in that mode against the float64 tolerances.
 Error bound of the digit Gram, per row and tile of 128 rows (Mx, My: the largest
 magnitudes of the two columns in the tile): a tile shares its column's fixed-point
 scale with the other tiles of its accumulation chunk only while its exponent maximum
-stays within two of the scale's, so every value is rounded to a multiple of at most
-2^-48 Mx (an error of at most 2^-49 Mx), and the dropped digit pairs (levels 8..12)
-weigh at most 5 * 2^14 * 2^32 / 2^98 < 2^-49 of Mx My, so
-|C - X^T Y|_ij <= 2^-47 sum_t 128 Mx My over the tiles t."""
+stays within two of the scale's, so every value is truncated to a multiple of at most
+2^-50 Mx, and the dropped digit pairs (levels 8..12) weigh at most 5 * 2^14 * 2^32 / 2^104
+< 2^-55 of Mx My, so |C - X^T Y|_ij <= 2^-48 sum_t 128 Mx My over the tiles t, within
+the 2^-47 the test allows."""
 import numpy as np
 import pytest
 
