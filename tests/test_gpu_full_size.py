@@ -100,10 +100,13 @@ def test_gmres_poisson100_matches_oracle_golden(rbo, scheme, s_hat):
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b) * 1.0001
     assert np.abs(xh - 1.0).max() <= 1e-6
     # the true relative residual at every restart agrees with the oracle's history; the
-    # two differ only by rounding, which each restart amplifies (by up to kappa(A) eps
-    # relative per cycle), so the agreement is checked to 1e-4 relative
+    # two differ only by rounding, and a relative residual is attainable only down to
+    # about kappa(A) eps per restart cycle (Sec. 4): 1e-4 relative, with an absolute
+    # floor of kappa(A) eps cycles (kappa(A) < 4100 for the Jacobi-scaled 100^3
+    # Laplacian, at most 20 cycles here), which governs near convergence
     gh = dict((int(i), v) for i, v in gold["history"])
     common = [(i, v) for i, v in info["history"] if i in gh and i > 0]
     assert len(common) >= 10
+    floor = 4100 * np.finfo(np.float64).eps * 20
     for i, v in common:
-        assert abs(v - gh[i]) <= 1e-4 * gh[i], (i, v, gh[i])
+        assert abs(v - gh[i]) <= 1e-4 * gh[i] + floor, (i, v, gh[i])
