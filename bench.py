@@ -193,6 +193,32 @@ def run_ours(args):
                 "one_stage": {"iterations": i1["iterations"], "relres": i1["relres"]},
                 "two_stage": {"iterations": i2["iterations"], "relres": i2["relres"]}}
 
+    # the same solves with the wide Gram passes on the tensor cores (RBO_PREC_OZAKI:
+    # exact digit products, float64 tolerances)
+    ozaki = None
+    if not args.no_ozaki:
+        def solve_oz(s_hat):
+            x.zero_()
+            _, info = rbo.sstep_gmres(Ad, bd, x, s=S, s_hat=s_hat, m=M, tol=TOL,
+                                      precision=rbo.PREC_OZAKI)
+            if info["status"] != 0:
+                raise RuntimeError(f"sstep_gmres ozaki failed: {info}")
+            return info
+        solve_oz(0)
+        solve_oz(S_HAT)
+        barrier()
+        z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        z0.record()
+        for _ in range(args.steps):
+            o1 = solve_oz(0)
+            o2 = solve_oz(S_HAT)
+        z1.record()
+        barrier()
+        zms = z0.elapsed_time(z1) / args.steps
+        ozaki = {"s_per_solve": zms / 2.0 / 1e3, "ms_per_step": zms,
+                 "one_stage": {"iterations": o1["iterations"], "relres": o1["relres"]},
+                 "two_stage": {"iterations": o2["iterations"], "relres": o2["relres"]}}
+
     # the two-stage solve with BCGS-PIP preprocessing (the paper's deterministic
     # two-stage comparator), same problem
     def solve_pip():
@@ -253,6 +279,7 @@ def run_ours(args):
                               "relres": two["relres"], "kernel_launches": two["kernel_launches"]},
             },
             "df64": df64,
+            "ozaki": ozaki,
             "two_stage_pip": pip,
             "ms_per_step_profiled": ms_prof,
             "kernels": prof,
@@ -368,7 +395,7 @@ def run_e2e(rbo, torch, A, b_host, args):
 
 
 ORTH_TOL = 1e-13   # the metric counts columns/s and GB/s only at ||I - Q^T Q||_2 <= 1e-13
-PREC_NAMES = ("fp64", "mixed", "df64")
+PREC_NAMES = ("fp64", "mixed", "df64", "ozaki")
 
 
 def _orth_bytes(scheme, c, s, s_hat, n):
@@ -434,7 +461,7 @@ def _orth_vs_oracle(rbo, torch, V0, c, s, s_hat, nrows=20000):
     out = []
     for scheme in ("one", "two"):
         ref = refs[scheme]
-        for prec in (rbo.PREC_FP64, rbo.PREC_MIXED, rbo.PREC_DF64):
+        for prec in (rbo.PREC_FP64, rbo.PREC_MIXED, rbo.PREC_DF64, rbo.PREC_OZAKI):
             Wd = rbo.colmajor(nrows, c)
             Wd.copy_(torch.from_numpy(Vh))
             o = _orth_call(rbo, sk, Wd, scheme, s, s_hat, prec)
@@ -480,7 +507,7 @@ def run_orth(rbo, torch, args):
         for scheme in ("two", "one", "two_pip"):
             R64 = None
             for prec in ((rbo.PREC_FP64,) if scheme == "two_pip" else
-                         (rbo.PREC_FP64, rbo.PREC_MIXED, rbo.PREC_DF64)):
+                         (rbo.PREC_FP64, rbo.PREC_MIXED, rbo.PREC_DF64, rbo.PREC_OZAKI)):
                 Wm = W.t()  # n x c column-major view
                 times = []
                 info = None
@@ -870,6 +897,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-prof", action="store_true")
     ap.add_argument("--no-df64", action="store_true")
+    ap.add_argument("--no-ozaki", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-full", action="store_true")
     ap.add_argument("--stress", action="store_true",

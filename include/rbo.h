@@ -68,16 +68,18 @@ extern "C" {
                               the sketch and the small factors in float64.  Only steps
                               that cannot reach the backward error ||V - QR|| are
                               moved off the float64 pipe                              */
-#define RBO_PREC_OZAKI  3  /* float64 data and results; the Gram matrices of the BCGS and
-                              CholQR reductions (passes with at most 64 columns of [X Y']
-                              and 8 of Y', no projection) are computed on the bf16 tensor
-                              cores from exact integer products: per tile of 128 rows
-                              every value is scaled by its column's largest power of two
-                              to a 55-bit integer, split into 7 balanced 8-bit digits
-                              (each exact in bf16), the digit products are summed exactly
-                              in float32 and the pairs of digit levels I + J <= 6 are
-                              combined in 64/128-bit integers (Ozaki, Ogita, Oishi and
-                              Rump 2012); every other step as RBO_PREC_FP64            */
+#define RBO_PREC_OZAKI  3  /* float64 data and results; the wide Gram matrices of the BCGS
+                              and CholQR reductions (passes of 36 to 64 columns of [X Y'],
+                              at most 8 of Y', no projection, no triangular solve) are
+                              computed on the fp16 tensor cores from exact integer
+                              products: per accumulation chunk of up to 1024 rows every
+                              value is scaled by a power of two of its column to an
+                              integer below 2^53, split into 7 balanced 8-bit digits
+                              (each exact in fp16), the digit products are summed
+                              exactly in float32 and the pairs of digit levels
+                              I + J <= 7 are combined in 64/128-bit integers (Ozaki,
+                              Ogita, Oishi and Rump 2012); every other pass as
+                              RBO_PREC_FP64                                           */
 
 /* ---- intra-block choice (one-stage) ----------------------------------------- */
 #define RBO_INTRA_RANDCHOLQR 0  /* RandCholQR (Figure 4b)                                */

@@ -44,7 +44,7 @@ ERR_LOST_ORTHOGONALITY = -9
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_DF64 = 2
-PREC_OZAKI = 3   # Gram passes as exact digit products on the bf16 tensor cores
+PREC_OZAKI = 3   # wide Gram passes as exact digit products on the fp16 tensor cores
 INTRA_RANDCHOLQR = 0
 INTRA_CHOLQR2 = 1
 STAGE_NAMES = {0: "", 1: "v0", 2: "intra", 3: "intra2", 4: "final", 5: "bigpanel", 6: "preproc"}

@@ -1,5 +1,5 @@
 """GPU parity of the tensor-core Gram (precision mode PREC_OZAKI: exact products of 8-bit
-digits on the bf16 tensor cores) against the oracle, and of the orthogonalization
+digits on the fp16 tensor cores) against the oracle, and of the orthogonalization
 schemes and s-step GMRES in that mode against the float64 tolerances.
 
 Error bound of the digit Gram, per row and tile of 128 rows (Mx, My: the largest
