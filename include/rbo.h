@@ -148,9 +148,10 @@ typedef struct rbo_info {
   int64_t resid_ld;
   int32_t resid_cap;
   int32_t resid_len;         /* residual columns written                              */
-  int32_t fallbacks;         /* GMRES, RBO_PREC_MIXED: restart cycles redone in float64
-                                after a block lost orthogonality or broke down (float64
-                                then stays on for the rest of the solve)               */
+  int32_t fallbacks;         /* RBO_PREC_MIXED: GMRES restart cycles, or blocks (two-stage:
+                                big panels) of a block orthogonalization, redone in
+                                float64 after a block lost orthogonality or broke down
+                                (float64 then stays on for the rest of the call)       */
 } rbo_info;
 
 /* ---- sparse-sign sketch (Section 3 / 5.2; the paper's Count sketch with zeta

@@ -363,10 +363,12 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   const int pmax = ncols;
   const int maxL = orth_max_L(pmax, kmax, rand ? std::max(sk->d, sk->d_inner) : 0);
   Arena* ar = nullptr;
+  const bool mixed = opts && opts->precision == RBO_PREC_MIXED;
   size_t bytes = reduction_bytes(maxL) +
                  orth_ctx_bytes(pmax, kmax, d, n, rand ? sk->zeta : 0, rand ? sk->type : 0,
                                 rand ? sk->d_inner : 0) +
                  (size_t)ncols * ncols * 8 + 4096;
+  if (mixed) bytes += (size_t)n * kmax * 8 + 256;  // copy of the block in flight
   if ((e = arena_prepare(&ar, bytes))) return info_done(info, e, 0, t0);
   if ((e = arena_reserve_reduction(ar, maxL, st))) return info_done(info, e, 0, t0);
   double* Rdev = (double*)ar->take((size_t)ncols * ncols * 8);
@@ -388,6 +390,36 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
     c.d_inner = sk->d_inner;
   }
   if ((e = orth_ctx_alloc(c, pmax, kmax, n))) return info_done(info, e, 0, t0);
+  // Mixed precision: a block (two-stage: a big panel) that the float32 steps could not
+  // precondition -- its final CholQR lost orthogonality or a Cholesky pivot broke down --
+  // is redone in float64 from a copy of its columns taken before it started, and float64
+  // stays on for the rest of the call (as in s-step GMRES).  In this mode every block
+  // ends with a status check (one synchronisation of the stream).
+  double* save = nullptr;
+  if (mixed && !(save = (double*)ar->take((size_t)n * kmax * 8))) return info_done(info, RBO_ERR_NOMEM, 0, t0);
+  int fallbacks = 0;
+  auto guarded = [&](int p0, int width, auto&& body) -> int {
+    double* Vb = V + (int64_t)p0 * ldv;
+    const bool guard = c.mixed != 0;
+    if (guard && cudaMemcpy2DAsync(save, (size_t)n * 8, Vb, (size_t)ldv * 8, (size_t)n * 8, width,
+                                   cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return note_cuda(cudaGetLastError());
+    int e2 = body();
+    if (e2 || !guard) return e2;
+    if ((e2 = note_cuda(cudaMemcpyAsync(ar->status_host, ar->status, sizeof(DevStatus),
+                                        cudaMemcpyDeviceToHost, st))))
+      return e2;
+    if ((e2 = note_cuda(cudaStreamSynchronize(st)))) return e2;
+    const int code = ar->status_host->code;
+    if (code != RBO_ERR_LOST_ORTHOGONALITY && code != RBO_ERR_CHOL_BREAKDOWN) return RBO_OK;
+    if ((e2 = note_cuda(cudaMemsetAsync(ar->status, 0, sizeof(DevStatus), st)))) return e2;
+    if ((e2 = note_cuda(cudaMemcpy2DAsync(Vb, (size_t)ldv * 8, save, (size_t)n * 8, (size_t)n * 8, width,
+                                          cudaMemcpyDeviceToDevice, st))))
+      return e2;
+    c.mixed = 0;
+    ++fallbacks;
+    return body();
+  };
   int p = 0;
   if (v0) {
     if ((e = normalise_column(c, n, V, Rdev, ncols, 0))) return info_done(info, e, c.launches, t0);
@@ -396,19 +428,25 @@ static int block_orth_impl(rbo_sketch sk, int64_t n, int32_t ncols, int32_t s, i
   if (scheme == 0) {
     int blk = 0;
     for (; p < ncols; p += s, ++blk) {
-      e = one_stage_block(c, n, V, ldv, p, V + (int64_t)p * ldv, ldv, s, intra, Rdev, ncols, p, blk);
+      e = guarded(p, s, [&]() {
+        return one_stage_block(c, n, V, ldv, p, V + (int64_t)p * ldv, ldv, s, intra, Rdev, ncols, p, blk);
+      });
+      if (info) info->fallbacks = fallbacks;
       if (e) return info_done(info, e, c.launches, t0);
     }
   } else {
     int blk = 0;
     for (; p < ncols; p += s_hat, ++blk) {
-      BigPanel bp;
-      bp.n = n; bp.Q = V; bp.ldq = ldv; bp.P = p;
-      bp.VB = V + (int64_t)p * ldv; bp.ldv = ldv; bp.K = s_hat; bp.blk = blk;
-      for (int j = 0; j < s_hat / s; ++j)
-        if ((e = bigpanel_add(c, bp, s))) return info_done(info, e, c.launches, t0);
-      if ((e = bigpanel_finish(c, bp, Rdev, ncols, p, nullptr, 0)))
-        return info_done(info, e, c.launches, t0);
+      e = guarded(p, s_hat, [&]() {
+        BigPanel bp;
+        bp.n = n; bp.Q = V; bp.ldq = ldv; bp.P = p;
+        bp.VB = V + (int64_t)p * ldv; bp.ldv = ldv; bp.K = s_hat; bp.blk = blk;
+        int e3 = RBO_OK;
+        for (int j = 0; j < s_hat / s && !e3; ++j) e3 = bigpanel_add(c, bp, s);
+        return e3 ? e3 : bigpanel_finish(c, bp, Rdev, ncols, p, nullptr, 0);
+      });
+      if (info) info->fallbacks = fallbacks;
+      if (e) return info_done(info, e, c.launches, t0);
     }
   }
   if ((e = copy_R_out(Rdev, ncols, R, ldr, st))) return info_done(info, e, c.launches, t0);
