@@ -5,8 +5,18 @@ TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this package; only
 legs of ``bench.py`` may use it.  It is a plain, slow, step-by-step restatement
 of the schemes of Yamazaki, Higgins, Boman and Szyld, "Random sketching to
 enhance the numerical stability of block orthogonalization algorithms for
-s-step GMRES" (arXiv 2503.16717), in float64 with numpy/scipy primitives.  It
-shares no code with the CUDA library.
+s-step GMRES" (arXiv 2503.16717), in float64.  It shares no code with the
+CUDA library.
+
+Two implementations of the same definitions: the numpy modules below, and a plain
+C++17 implementation in ``cpp/`` (loops over column-major float64 arrays, no BLAS;
+built by ``build_cpp.py``, bound by ``cpp_oracle.py``) of the sketch, the dense
+kernels, the accuracy measures, the one-stage and two-stage schemes, CSR SpMV,
+s-step GMRES with the monomial basis and Householder GMRES.  The GPU parity tests of
+the orthogonalization schemes and ``smoke()`` check against the C++ one; the numpy
+one covers what the C++ one does not (Newton and Chebyshev bases, Gaussian and
+Count-Gauss sketch schemes, the learned preconditioner), and the two are checked
+against each other in ``tests/test_oracle_cpp.py``.
 
 Modules
 -------
