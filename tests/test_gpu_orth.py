@@ -32,14 +32,15 @@ def run(rbo, scheme, V, s, s_hat=None, v0=False, precision=0, d=None):
 
 
 def oracle(scheme, V, s, s_hat=None, v0=False, d=None):
+    """The C++ oracle's result for the same input and sketch (Q, R, ok, breakdown)."""
+    from oracle import cpp_oracle as cpp
     n, c = V.shape
     d = d or 4 * (c + 1 - (1 if v0 else 0) + (1 if v0 else 0))
-    sk = OSketch(n, d, 8, 42)
     if scheme == "one":
-        return orth.block_orth_one_stage(V, s, sk, v0=v0)
+        return cpp.block_orth_one_stage(V, s, d=d, v0=v0)
     if scheme == "two":
-        return orth.block_orth_two_stage(V, s, s_hat, sk, v0=v0)
-    return orth.block_orth_cholqr2(V, s, v0=v0)
+        return cpp.block_orth_two_stage(V, s, s_hat, d=d, v0=v0)
+    return cpp.block_orth_one_stage(V, s, intra="cholqr2", v0=v0)
 
 
 @pytest.mark.parametrize("scheme,s_hat", [("one", None), ("two", 30), ("two", 10), ("cholqr2", None)])
@@ -203,7 +204,8 @@ def test_two_stage_pip_matches_oracle(rbo, n, s_hat):
     Vd = to_dev(V)
     out = rbo.block_orth_two_stage(None, Vd, 5, s_hat, v0=True, preproc=rbo.PREPROC_PIP)
     Q = to_host(Vd)
-    ref = orth.block_orth_two_stage(V, 5, s_hat, None, v0=True, preproc="pip")
+    from oracle import cpp_oracle as cpp
+    ref = cpp.block_orth_two_stage(V, 5, s_hat, v0=True, preproc="pip")
     assert out.info["status"] == 0 and ref.ok
     assert metrics.rel_diff(out.R, ref.R) <= 1e-12
     assert np.abs(Q - ref.Q).max() <= 1e-9
