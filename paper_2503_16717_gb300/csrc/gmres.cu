@@ -59,6 +59,13 @@ struct GmresWork {
   double* Rdev;     // (m+1) x (m+1)
   double* coords;   // (m+1) x s_hat
   double* bn;       // 1 (||b||^2)
+  // SELL-32 copy of the MPK operator (short rows, no separate M): slot offsets, slice
+  // widths, indices and values
+  int64_t* sell_off;
+  int32_t* sell_w;
+  int32_t* sell_col;
+  double* sell_val;
+  int64_t sell_cap;
 };
 
 int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, double* x, int s,
@@ -81,6 +88,12 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   size_t bytes = reduction_bytes(maxL) + orth_ctx_bytes(pmax, kmax, d, n, zeta, sk_type, d_inner) +
                  (size_t)ldq * (m + 1) * 8 + (size_t)A->nnz * 8 + 2 * (size_t)n * 8 +
                  (size_t)(m + 1) * (m + 1) * 8 + (size_t)(m + 1) * K * 8 + (size_t)m * 8 + 16 * 1024;
+  // the MPK operator in SELL-32 form when its rows are short (stencils): room for the
+  // stored entries plus two padding slots per row on average
+  const bool use_sell = precond != 2 && n > 0 && (double)A->nnz <= 12.0 * (double)n;
+  const int64_t nsl = (n + 31) / 32;
+  const int64_t sell_cap = use_sell ? A->nnz + 2 * n + 64 : 0;
+  if (use_sell) bytes += (size_t)sell_cap * 12 + (size_t)(nsl + 1) * 8 + (size_t)nsl * 4 + 1024;
   Arena* ar = nullptr;
   int e = arena_prepare(&ar, bytes);
   if (e) return e;
@@ -96,6 +109,12 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
   w.Rdev = (double*)ar->take((size_t)ld * ld * 8);
   w.coords = (double*)ar->take((size_t)ld * K * 8);
   w.bn = (double*)ar->take(64);
+  w.sell_cap = sell_cap;
+  w.sell_off = use_sell ? (int64_t*)ar->take((size_t)(nsl + 1) * 8) : nullptr;
+  w.sell_w = use_sell ? (int32_t*)ar->take((size_t)nsl * 4) : nullptr;
+  w.sell_col = use_sell ? (int32_t*)ar->take((size_t)sell_cap * 4) : nullptr;
+  w.sell_val = use_sell ? (double*)ar->take((size_t)sell_cap * 8) : nullptr;
+  if (use_sell && (!w.sell_off || !w.sell_w || !w.sell_col || !w.sell_val)) return RBO_ERR_NOMEM;
   if (!w.Qb || !w.t1 || !w.t2 || !w.zdev || !w.Rdev || !w.coords || !w.bn ||
       (precond == 1 && (!w.vals || !w.dscale)))
     return RBO_ERR_NOMEM;
@@ -125,6 +144,12 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
     Ahat.val = w.vals;
     c.launches += 2;
   }
+  SellDev sell;
+  if (use_sell) {
+    if ((e = sell_build(Ahat, w.sell_cap, w.sell_off, w.sell_w, w.sell_col, w.sell_val, ar->status, st, &sell)))
+      return e;
+    if (sell.n > 0) c.launches += 2;
+  }
   // out = A M u: one SpMV with the column-scaled values (Jacobi), two SpMVs (M given),
   // or one SpMV with A (no preconditioner)
   // out = A M u (+ the basis shift of `sh`, fused into the last SpMV)
@@ -137,6 +162,7 @@ int sstep_gmres_impl(const rbo_csr* A, const double* Mval, const double* b, doub
       return RBO_OK;
     }
     c.launches += 1;
+    if (sell.n > 0) return spmv_sell_launch(sell, Ahat.nnz, u, out, st, sh);
     return spmv_launch(Ahat, nullptr, u, out, ar->status, st, sh);
   };
   // ||b||

@@ -219,6 +219,24 @@ struct SpmvShift {
 // Invalid indices are skipped and reported in `status` (may be null).
 int spmv_launch(const CsrDev& A, const double* dscale, const double* x, double* y,
                 DevStatus* status, cudaStream_t st, const SpmvShift& sh = SpmvShift());
+// Sliced ELL copy of a CSR matrix with short rows (SELL-32): slices of 32 consecutive
+// rows, each slice padded to its longest row; slot j of row 32 k + l at
+// soff[k] + 32 j + l, padding slots hold the row's own index and the value 0.
+struct SellDev {
+  int64_t n = 0, nslices = 0;    // n = 0: not built
+  const int64_t* soff = nullptr; // nslices + 1 slot offsets
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+};
+// Slots needed by the SELL-32 copy of A if its padding stays within `cap_slots`:
+// builds it into (soff, col, val) and fills *out, else leaves out->n = 0.  Column
+// indices outside [0, n) and malformed row pointers are reported in `status` (and
+// stored as zero entries).  One host synchronisation (the slice widths).
+int sell_build(const CsrDev& A, int64_t cap_slots, int64_t* soff, int32_t* width_scratch, int32_t* col,
+               double* val, DevStatus* status, cudaStream_t st, SellDev* out);
+// y = A x with the optional shift, from the SELL-32 copy
+int spmv_sell_launch(const SellDev& S, int64_t nnz, const double* x, double* y, cudaStream_t st,
+                     const SpmvShift& sh = SpmvShift());
 // r = b - A x  (A already scaled if needed)
 int residual_launch(const CsrDev& A, const double* b, const double* x, double* r, DevStatus* status,
                     cudaStream_t st);

@@ -9,6 +9,9 @@
 // diagonal scaling D of the right Jacobi preconditioner (A D x) is applied to the
 // gathered x entries; the optional shift terms of the Newton and Chebyshev bases
 // are added to each output row.
+#include <algorithm>
+#include <vector>
+
 #include "device_common.cuh"
 
 namespace rbo {
@@ -313,6 +316,164 @@ int scale_vec_launch(int64_t n, const double* dscale, const double* y, double* x
                      cudaStream_t st) {
   if (n <= 0) return RBO_OK;
   scale_vec_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, dscale, y, x, mode);
+  return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
+}
+
+}  // namespace rbo
+
+namespace rbo {
+
+// ---- SELL-32: the short-row matrices of the MPK in sliced ELL form -------------------
+// A warp owns a slice of 32 rows and a lane its row: slot j of the slice is one
+// coalesced 256-byte value load and 128-byte index load for the whole warp, and the
+// slots of a row are summed in two interleaved chains (even, odd j) added at the end, a
+// fixed order.  Padding slots (value 0, the row's own index) cost a multiply-add.
+
+__global__ void sell_width_kernel(int64_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
+                                  int32_t* __restrict__ width, DevStatus* status) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t k = t >> 5;
+  const int lane = (int)(t & 31);
+  const int64_t nsl = (n + 31) / 32;
+  if (k >= nsl) return;  // whole warps (nsl * 32 threads are launched)
+  const int64_t r = k * 32 + lane;
+  int len = 0;
+  if (r < n) {
+    const int beg = rowptr[r], end = rowptr[r + 1];
+    if (beg < 0 || end < beg || (int64_t)end > nnz) {
+      if (status) set_error(status, RBO_ERR_ARG, 11);
+    } else {
+      len = end - beg;
+    }
+  }
+  len = __reduce_max_sync(0xffffffffu, len);
+  if (lane == 0) width[k] = len;
+}
+
+__global__ void sell_fill_kernel(int64_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ ccol, const double* __restrict__ cval,
+                                 const int64_t* __restrict__ soff, int32_t* __restrict__ col,
+                                 double* __restrict__ val, DevStatus* status) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t k = t >> 5;
+  const int lane = (int)(t & 31);
+  if (k >= (n + 31) / 32) return;
+  const int64_t r = k * 32 + lane;
+  const int64_t off = soff[k];
+  const int w = (int)((soff[k + 1] - off) / 32);
+  int beg = 0, len = 0;
+  if (r < n) {
+    beg = rowptr[r];
+    const int end = rowptr[r + 1];
+    if (beg >= 0 && end >= beg && (int64_t)end <= nnz) len = end - beg;
+  }
+  const int32_t self = (int32_t)(r < n ? r : 0);
+  for (int j = 0; j < w; ++j) {
+    int32_t c = self;
+    double v = 0.0;
+    if (j < len) {
+      const int32_t cj = ccol[beg + j];
+      if (cj < 0 || (int64_t)cj >= n) {
+        if (status) set_error(status, RBO_ERR_ARG, 12);
+      } else {
+        c = cj;
+        v = cval[beg + j];
+      }
+    }
+    col[off + (int64_t)j * 32 + lane] = c;
+    val[off + (int64_t)j * 32 + lane] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) spmv_sell_kernel(int64_t n, int64_t nsl, const int64_t* __restrict__ soff,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const double* __restrict__ x, double* __restrict__ y,
+                                                        SpmvShift sh) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); k < nsl; k += warps) {
+    const int64_t off = __ldg(soff + k);
+    const int w = (int)((__ldg(soff + k + 1) - off) >> 5);
+    const int32_t* cp = col + off + lane;
+    const double* vp = val + off + lane;
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 4 <= w; j += 4) {
+      const int32_t c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
+      const int32_t c2 = __ldg(cp + 32 * (j + 2)), c3 = __ldg(cp + 32 * (j + 3));
+      const double v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
+      const double v2 = __ldg(vp + 32 * (j + 2)), v3 = __ldg(vp + 32 * (j + 3));
+      s0 = fma(v0, __ldg(x + c0), s0);
+      s1 = fma(v1, __ldg(x + c1), s1);
+      s0 = fma(v2, __ldg(x + c2), s0);
+      s1 = fma(v3, __ldg(x + c3), s1);
+    }
+    for (; j < w; ++j) {
+      const double v = __ldg(vp + 32 * j), xv = __ldg(x + __ldg(cp + 32 * j));
+      if (j & 1) s1 = fma(v, xv, s1);
+      else s0 = fma(v, xv, s0);
+    }
+    const int64_t r = k * 32 + lane;
+    if (r < n) y[r] = shifted(s0 + s1, sh, r);
+  }
+}
+
+}  // namespace rbo
+
+namespace rbo {
+
+int sell_build(const CsrDev& A, int64_t cap_slots, int64_t* soff, int32_t* width, int32_t* col,
+               double* val, DevStatus* status, cudaStream_t st, SellDev* out) {
+  *out = SellDev();
+  if (A.n <= 0) return RBO_OK;
+  const int64_t nsl = (A.n + 31) / 32;
+  const int64_t threads = nsl * 32;
+  sell_width_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A.n, A.nnz, A.rowptr, width, status);
+  if (cudaGetLastError() != cudaSuccess) return RBO_ERR_CUDA;
+  std::vector<int32_t> wh((size_t)nsl);
+  std::vector<int64_t> oh((size_t)nsl + 1);
+  if (cudaMemcpyAsync(wh.data(), width, (size_t)nsl * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RBO_ERR_CUDA;
+  oh[0] = 0;
+  for (int64_t k = 0; k < nsl; ++k) oh[(size_t)k + 1] = oh[(size_t)k] + 32 * (int64_t)wh[(size_t)k];
+  if (oh[(size_t)nsl] > cap_slots) return RBO_OK;  // too much padding: stay with CSR
+  if (cudaMemcpyAsync(soff, oh.data(), (size_t)(nsl + 1) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return RBO_ERR_CUDA;
+  sell_fill_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A.n, A.nnz, A.rowptr, A.col, A.val, soff,
+                                                                      col, val, status);
+  if (cudaGetLastError() != cudaSuccess) return RBO_ERR_CUDA;
+  // the host copy of the offsets must outlive the asynchronous upload
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RBO_ERR_CUDA;
+  out->n = A.n;
+  out->nslices = nsl;
+  out->soff = soff;
+  out->col = col;
+  out->val = val;
+  return RBO_OK;
+}
+
+int spmv_sell_launch(const SellDev& S, int64_t nnz, const double* x, double* y, cudaStream_t st,
+                     const SpmvShift& sh) {
+  if (S.n <= 0) return RBO_OK;
+  SpmvShift k = sh;
+  if (!k.u) k = SpmvShift();
+  if (k.b == 0.0) k.uprev = nullptr;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int64_t blocks = std::min<int64_t>((S.nslices + 7) / 8, (int64_t)sms * 8);
+  ProfToken tok = prof_start(st);
+  spmv_sell_kernel<<<(unsigned)blocks, 256, 0, st>>>(S.n, S.nslices, S.soff, S.col, S.val, x, y, k);
+  // algorithmic bytes and flops as for the CSR kernel (the stored entries, not the padding)
+  const double nn = (double)S.n, nz = (double)nnz;
+  const int terms = (k.u ? 1 : 0) + (k.uprev ? 1 : 0);
+  prof_stop(tok, st, 1, 12.0 * nz + 4.0 * (nn + 1) + 16.0 * nn + 8.0 * terms * nn, 2.0 * nz + 2.0 * terms * nn);
   return cudaGetLastError() == cudaSuccess ? RBO_OK : RBO_ERR_CUDA;
 }
 
