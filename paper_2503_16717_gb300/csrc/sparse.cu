@@ -385,38 +385,46 @@ __global__ void sell_fill_kernel(int64_t n, int64_t nnz, const int32_t* __restri
   }
 }
 
-__global__ void __launch_bounds__(256) spmv_sell_kernel(int64_t n, int64_t nsl, const int64_t* __restrict__ soff,
-                                                        const int32_t* __restrict__ col,
-                                                        const double* __restrict__ val,
-                                                        const double* __restrict__ x, double* __restrict__ y,
-                                                        SpmvShift sh) {
+__global__ void __launch_bounds__(256, 6) spmv_sell_kernel(int64_t n, int64_t nsl, const int64_t* __restrict__ soff,
+                                                           const int32_t* __restrict__ col,
+                                                           const double* __restrict__ val,
+                                                           const double* __restrict__ x, double* __restrict__ y,
+                                                           SpmvShift sh) {
+  // one slice per warp (the grid covers the matrix): every warp's loads are in flight
+  // at once; slices of up to 8 slots load all indices and values before the gathers
   const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); k < nsl; k += warps) {
-    const int64_t off = __ldg(soff + k);
-    const int w = (int)((__ldg(soff + k + 1) - off) >> 5);
-    const int32_t* cp = col + off + lane;
-    const double* vp = val + off + lane;
-    double s0 = 0.0, s1 = 0.0;
-    int j = 0;
-    for (; j + 4 <= w; j += 4) {
-      const int32_t c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
-      const int32_t c2 = __ldg(cp + 32 * (j + 2)), c3 = __ldg(cp + 32 * (j + 3));
-      const double v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
-      const double v2 = __ldg(vp + 32 * (j + 2)), v3 = __ldg(vp + 32 * (j + 3));
-      s0 = fma(v0, __ldg(x + c0), s0);
-      s1 = fma(v1, __ldg(x + c1), s1);
-      s0 = fma(v2, __ldg(x + c2), s0);
-      s1 = fma(v3, __ldg(x + c3), s1);
+  const int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= nsl) return;
+  const int64_t off = __ldg(soff + k);
+  const int w = (int)((__ldg(soff + k + 1) - off) >> 5);
+  const int32_t* cp = col + off + lane;
+  const double* vp = val + off + lane;
+  double s0 = 0.0, s1 = 0.0;
+  if (w <= 8) {
+    int32_t c[8];
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c[j] = j < w ? __ldg(cp + 32 * j) : 0;
+      v[j] = j < w ? __ldg(vp + 32 * j) : 0.0;
     }
-    for (; j < w; ++j) {
-      const double v = __ldg(vp + 32 * j), xv = __ldg(x + __ldg(cp + 32 * j));
-      if (j & 1) s1 = fma(v, xv, s1);
-      else s0 = fma(v, xv, s0);
+    double xv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) xv[j] = j < w ? __ldg(x + c[j]) : 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      if (j < w) s0 = fma(v[j], xv[j], s0);
+      if (j + 1 < w) s1 = fma(v[j + 1], xv[j + 1], s1);
     }
-    const int64_t r = k * 32 + lane;
-    if (r < n) y[r] = shifted(s0 + s1, sh, r);
+  } else {
+    for (int j = 0; j < w; ++j) {
+      const double vv = __ldg(vp + 32 * j), xx = __ldg(x + __ldg(cp + 32 * j));
+      if (j & 1) s1 = fma(vv, xx, s1);
+      else s0 = fma(vv, xx, s0);
+    }
   }
+  const int64_t r = k * 32 + lane;
+  if (r < n) y[r] = shifted(s0 + s1, sh, r);
 }
 
 }  // namespace rbo
@@ -460,14 +468,8 @@ int spmv_sell_launch(const SellDev& S, int64_t nnz, const double* x, double* y, 
   SpmvShift k = sh;
   if (!k.u) k = SpmvShift();
   if (k.b == 0.0) k.uprev = nullptr;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  const int64_t blocks = std::min<int64_t>((S.nslices + 7) / 8, (int64_t)sms * 8);
+  const int64_t blocks = (S.nslices + 7) / 8;
+  if (blocks > 0x7FFFFFFFLL) return RBO_ERR_ARG;
   ProfToken tok = prof_start(st);
   spmv_sell_kernel<<<(unsigned)blocks, 256, 0, st>>>(S.n, S.nslices, S.soff, S.col, S.val, x, y, k);
   // algorithmic bytes and flops as for the CSR kernel (the stored entries, not the padding)
