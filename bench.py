@@ -127,6 +127,7 @@ def run_ours(args):
 
     A = synth.poisson3d_csr(N_GRID)
     b_host = synth.ones_rhs(A)
+    args.n_rows = A.n
     Ad = rbo.DeviceCSR.from_host(A)
     bd = torch.from_numpy(b_host).cuda()
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
@@ -299,10 +300,12 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def measured_traffic():
-    """DRAM bytes per row-pass launch from the committed ncu capture of this
-    workload (profiles/rowpass_traffic.json), or None when the kernel source has
-    changed since the counters were taken."""
+def measured_traffic(passes, n, launches):
+    """DRAM bytes per row-pass launch of the step, from the committed one-kernel captures
+    of the two row-pass instances (profiles/rowpass_traffic.json): the Gram instance's
+    DRAM/algorithmic ratio applied to the roles without a sketch, and for the update +
+    sketch roles their algorithmic bytes plus the measured schedule-record bytes per row.
+    None when the row-pass source has changed since the counters were taken."""
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
     try:
@@ -312,9 +315,17 @@ def measured_traffic():
             sha = hashlib.sha256(f.read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if rec.get("rowpass_cu_sha256") != sha:
+    if rec.get("rowpass_cu_sha256") != sha or not launches:
         return None
-    return rec.get("dram_bytes_per_launch")
+    ratio = rec["instances"]["gram"]["ratio"]
+    per_row = rec["instances"]["update_sketch"]["schedule_record_bytes_per_row"]
+    total = 0.0
+    for name, r in passes.items():
+        if "update_sketch" in name:
+            total += r["bytes"] + per_row * n * r["launches"]
+        else:
+            total += ratio * r["bytes"]
+    return total / launches
 
 
 def profile_steps(rbo, torch, step, barrier, args):
@@ -351,7 +362,9 @@ def profile_steps(rbo, torch, step, barrier, args):
                 "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_DERIVED / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_DERIVED,
                 "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 1.25 TFLOP/s nominal)",
-                "traffic": measured_traffic(), "launches": rp["launches"], "avg_launch_us": avg_ms * 1e3,
+                "traffic": measured_traffic(passes, args.n_rows, rp["launches"]),
+                "traffic_src": "estimated from one-kernel captures (profiles/rowpass_traffic.json)",
+                "launches": rp["launches"], "avg_launch_us": avg_ms * 1e3,
                 "hbm_gbs_algorithmic": rp["bytes"] / (rp["ms"] / 1e3) / 1e9 if rp["ms"] > 0 else 0.0,
                 "share_of_step": rp["ms"] / args.steps / ms_prof if ms_prof > 0 else None}
 
