@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "librbo.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"{LIB_PATH} is missing: build the CUDA library first "
-        "(python -c 'import __graft_entry__ as g; g.build()' or python -m paper_2503_16717_gb300.build)")
+        "(python -c 'import __graft_entry__ as g; g.build()' or python paper_2503_16717_gb300/build.py)")
 
 lib = C.CDLL(LIB_PATH)
 

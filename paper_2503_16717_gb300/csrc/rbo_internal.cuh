@@ -177,6 +177,14 @@ int ozaki_gram_launch(const RowPass& rp, Arena* ar, cudaStream_t st, int* launch
 // Enqueue one row pass; `launches` is incremented per kernel.  Returns RBO_OK or an
 // error for invalid sizes / CUDA launch failures.
 int rowpass_launch(const RowPass& rp, Arena* ar, cudaStream_t st, int* launches);
+// The sketch-scatter pass (rowpass_sk.cu), called by rowpass_launch for a pass with a
+// scattered sketch once the common checks passed: `L` partial length (d * b), `mixed`
+// float32 sketch sums.
+int rowpass_sk_launch(const RowPass& rp, Arena* ar, cudaStream_t st, int* launches, int num_sms,
+                      int L, int mixed);
+// Shared-memory bytes of its streaming loop for a X columns, b panel columns, T-row
+// tiles and a d-row, zeta-entry sparse sketch (with a projection and a triangle).
+size_t rowpass_sk_loop_bytes(int a, int b, int T, int d, int zeta);
 
 // Sketch schedule: S restricted to each tile of T basis rows, transposed once per
 // call so that the row pass needs neither hashing nor a scatter with conflicts.

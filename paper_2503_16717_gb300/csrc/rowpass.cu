@@ -1,23 +1,26 @@
 // The row pass: one fused streaming pass over the rows of a tall-skinny panel.
 //
-// Every step of the block orthogonalization that touches n-row data is an
-// instance of this kernel (BCGS Gram and update, sketch apply, the TRSMs of
-// CholQR/RandHH, the forward substitution of RandBCGS2 and the Gram matrices
-// feeding the Cholesky factorisations; Sections 4-7 of the paper):
+// Every step of the block orthogonalization that touches n-row data is a row pass
+// (BCGS Gram and update, sketch apply, the TRSMs of CholQR/RandHH, the forward
+// substitution of RandBCGS2 and the Gram matrices feeding the Cholesky
+// factorisations; Sections 4-7 of the paper):
 //
 //   per row r:   y'_r = (y_r - x_r C) Tri^{-1}      (or y_r Tri^{-1} - x_r C)
 //                write y'_r back to Y                     (optional)
 //                Z   += [x_r, y'_r]^T y'_r                (X^T Y' and/or Y'^T Y')
 //                SK  += s_r y'_r  (sketch column s_r: zeta entries +-1, hashed)
 //
+// This file holds the kernel of the passes without a scattered sketch (Gram and
+// transform passes) and the launcher of all row passes; the sketch passes run in
+// rowpass_sk.cu, the tensor-core Gram in ozaki.cu.
+//
 // Row tiles of T rows are staged in shared memory by the bulk-copy (TMA) engine
 // (cp.async.bulk + mbarrier, double buffered; ragged tiles use plain loads).
 // Each CTA owns a fixed set of tiles, keeps its partial Z in registers (one
-// output per thread slot) and its partial sketch in per-warp shared copies, then
-// writes one partial.  A two-level ticketed tree (groups of 16 CTAs, then one
-// top reducer) sums the partials in a fixed order, so results are bitwise
-// reproducible; the last CTA runs the small dense epilogue (Cholesky, Householder,
-// sketched BCGS2-HH, R assembly) on the reduced values.
+// output per thread slot), then writes one partial.  A two-level ticketed tree
+// (groups of 16 CTAs, then one top reducer) sums the partials in a fixed order, so
+// results are bitwise reproducible; the last CTA runs the small dense epilogue
+// (Cholesky, Householder, sketched BCGS2-HH, R assembly) on the reduced values.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -60,81 +63,20 @@ __device__ __forceinline__ void gram_rows_df(df (&acc)[CB], const df* z, const d
     for (int c = 0; c < CW; ++c) df_fma_acc(acc[c], zv, y[(size_t)c * TP + rr]);
   }
 }
-// Sketch of one sketch row over a tile, float64 path: the tile's values of each column
-// are held as int64 fixed point (unit 2^(E_c - 1077), E_c the column's largest
-// exponent field in the tile; fix_from_double); the row's entries are summed exactly
-// in integers (signs by integer negation), and the exact tile sum is rounded once to
-// float64 and added to the accumulator: one float64 add per (sketch row, column) and
-// tile instead of one per entry, on every lane.  A column with a non-finite value in
-// the tile (E_c = 0x7FF) makes the accumulators NaN.
-template <int CW>
-__device__ __forceinline__ void sketch_row_fix(double* acc, int d, const long long* y, int TP,
-                                               const int* emax, const uint8_t* e, int cnt) {
-  long long v[CW];
-#pragma unroll
-  for (int c = 0; c < CW; ++c) v[c] = 0;
-  for (int t = 0; t < cnt; ++t) {
-    const int ev = e[t];
-    const int r = ev >> 1;
-    const long long ng = -(long long)(ev & 1);  // 0 or all ones
-#pragma unroll
-    for (int c = 0; c < CW; ++c) {
-      const long long f = y[(size_t)c * TP + r];
-      v[c] += (f ^ ng) - ng;                     // f or -f
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < CW; ++c) {
-    const double add = emax[c] == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
-                                        : double_from_fix(v[c], emax[c]);
-    acc[(size_t)c * d] += add;
-  }
-}
-// float32 values in the first 4 bytes of each 8-byte slot: y holds 2 floats per row
-template <int CW>
-__device__ __forceinline__ void sketch_row_f32(float* acc, int d, const float* y, int TP2,
-                                               const uint8_t* e, int cnt) {
-  float v[CW];
-#pragma unroll
-  for (int c = 0; c < CW; ++c) v[c] = acc[(size_t)c * d];
-  for (int t = 0; t < cnt; ++t) {
-    const int ev = e[t];
-    const int r = 2 * (ev >> 1);
-    const int sg = (ev & 1) << 31;
-#pragma unroll
-    for (int c = 0; c < CW; ++c) v[c] += __int_as_float(__float_as_int(y[(size_t)c * TP2 + r]) ^ sg);
-  }
-#pragma unroll
-  for (int c = 0; c < CW; ++c) acc[(size_t)c * d] = v[c];
-}
-#define RBO_CW_DISPATCH(fn, cw, ...)            \
-  switch (cw) {                                 \
-    case 8: fn<8>(__VA_ARGS__); break;          \
-    case 7: fn<7>(__VA_ARGS__); break;          \
-    case 6: fn<6>(__VA_ARGS__); break;          \
-    case 5: fn<5>(__VA_ARGS__); break;          \
-    case 4: fn<4>(__VA_ARGS__); break;          \
-    case 3: fn<3>(__VA_ARGS__); break;          \
-    case 2: fn<2>(__VA_ARGS__); break;          \
-    default: fn<1>(__VA_ARGS__); break;         \
-  }
-
 // ------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------
-template <int ARITH, bool SK>
-__global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_kernel(const __grid_constant__ PassDev P) {
-  // ARITH 0: float64; 1: float32 for X^T Y' and the sketch (mixed precision);
-  // 2: float32 pairs for the transform and the Gram, float64 for the sketch.
-  // SK: the pass scatters a sparse sketch (and has no Gram); separate instances keep
-  // each loop's registers to itself.
+template <int ARITH>
+__global__ void __launch_bounds__(NT, (ARITH == 0 ? 3 : 2)) rowpass_kernel(const __grid_constant__ PassDev P) {
+  // ARITH 0: float64; 1: float32 for X^T Y' (mixed precision); 2: float32 pairs for
+  // the transform and the Gram.  Passes that scatter a sparse sketch run in
+  // rowpass_sk_kernel (rowpass_sk.cu).
   constexpr bool MIXED = ARITH == 1;
   constexpr bool DF = ARITH == 2;
   constexpr int IPTA = DF ? 2 : IPT;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_flag;
   __shared__ int s_last;
-  __shared__ int s_emax[64];  // sketch: largest exponent field per column of the tile
   const RowPass& rp = P.p;
   if (read_code(P.status) != 0) return;
 
@@ -148,11 +90,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
   double* Cs = reinterpret_cast<double*>(smem + P.off_c);
   double* Ts = reinterpret_cast<double*>(smem + P.off_tri);
   double* dinv = reinterpret_cast<double*>(smem + P.off_dinv);
-  double* skd = reinterpret_cast<double*>(smem + P.off_sk);
   double* gth = reinterpret_cast<double*>(smem + P.off_gth);  // Gaussian sketch tile
-  float* skf = reinterpret_cast<float*>(smem + P.off_sk);
-  const int d = rp.sk_d;
-  const bool do_sk = SK && d > 0;
 
   // small matrices + sketch copies
   if (rp.C) {
@@ -172,13 +110,6 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
       Ts[t] = (i <= c) ? rp.Tri[i + (size_t)c * ldt] : 0.0;
     }
     for (int t = tid; t < b; t += NT) dinv[t] = 1.0 / rp.Tri[t + (size_t)t * ldt];
-  }
-  if (do_sk) {
-    const int tot = d * b;
-    if (MIXED)
-      for (int t = tid; t < tot; t += NT) skf[t] = 0.0f;
-    else
-      for (int t = tid; t < tot; t += NT) skd[t] = 0.0;
   }
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
@@ -221,8 +152,6 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
     return reinterpret_cast<double*>(smem + P.off_stage + (size_t)s * P.stage_bytes);
   };
   auto stage_Y = [&](int s) { return stage_X(s) + (size_t)a * TP; };
-  auto stage_R = [&](int s) { return smem + P.off_stage + (size_t)s * P.stage_bytes + P.rec_off; };
-  const int rec_n = do_sk ? rp.sk.rec_bytes : 0;  // schedule record bytes per tile
 
   // bulk-copy a full tile into stage s (all lanes of warp 0: one copy per lane)
   auto issue_tile = [&](int tile, int s) {
@@ -230,16 +159,13 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
     double* xs = stage_X(s);
     double* ys = stage_Y(s);
     const uint32_t bytes = (uint32_t)T * 8u;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile + (uint32_t)rec_n);
+    if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes * (uint32_t)ncol_tile);
     __syncwarp();
-    const int ncopy = a + b + (rec_n > 0 ? 1 : 0);
-    for (int j = lane; j < ncopy; j += 32) {
+    for (int j = lane; j < a + b; j += 32) {
       if (j < a)
         bulk_copy_g2s(xs + (size_t)j * TP, rp.X + j * rp.ldx + r0, bytes, &bars[s]);
-      else if (j < a + b)
-        bulk_copy_g2s(ys + (size_t)(j - a) * TP, rp.Y + (j - a) * rp.ldy + r0, bytes, &bars[s]);
       else
-        bulk_copy_g2s(stage_R(s), rp.sk.rec + (size_t)tile * rec_n, (uint32_t)rec_n, &bars[s]);
+        bulk_copy_g2s(ys + (size_t)(j - a) * TP, rp.Y + (j - a) * rp.ldy + r0, bytes, &bars[s]);
     }
   };
   auto bulk_ok = [&](int tile) {
@@ -271,9 +197,6 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
         if (r < rows) v = (col < a) ? rp.X[col * rp.ldx + r0 + r] : rp.Y[(col - a) * rp.ldy + r0 + r];
         xs[(size_t)col * TP + r] = v;  // X and Y stages are contiguous
       }
-      uint32_t* es = reinterpret_cast<uint32_t*>(stage_R(s));
-      const uint32_t* eg = reinterpret_cast<const uint32_t*>(rp.sk.rec + (size_t)tile * rec_n);
-      for (int t = tid; t < rec_n / 4; t += NT) es[t] = eg[t];
       __syncthreads();
     }
     if (timed_out) {
@@ -396,7 +319,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
     }
 
     // ---- phase B: Gram outputs Z = [X, Y']^T Y' --------------------------------
-    if (MIXED && (P.no > 0 || do_sk)) {
+    if (MIXED && P.no > 0) {
       // float32 copies of the tile (integer-ALU conversion) in place: the float for
       // element t sits in the first 4 bytes of its double slot
       __syncthreads();
@@ -407,7 +330,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
       }
       __syncthreads();
     }
-    if (!SK && DF && P.no > 0) {
+    if (DF && P.no > 0) {
 #pragma unroll
       for (int k = 0; k < IPTA; ++k) {
         const int task = tid + k * NT;
@@ -427,7 +350,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
         flush();
         since_flush = 0;
       }
-    } else if (!SK && P.no > 0) {
+    } else if (P.no > 0) {
 #pragma unroll
       for (int k = 0; k < IPTA; ++k) {
         const int task = tid + k * NT;
@@ -445,65 +368,6 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
             RBO_CW_DISPATCH(gram_rows_f32, cw, accf[k], zsrc, ysrc, g, T, P.tpo, TP)
           } else {
             RBO_CW_DISPATCH(gram_rows_f64, cw, acc[k], zsrc, ysrc, g, T, P.tpo, TP)
-          }
-        }
-      }
-    }
-    // ---- phase B': sketch S Y' ---------------------------------------------------
-    // The tile's schedule record lists its non-empty sketch rows, most entries
-    // first; thread q takes slots q, q + NT, ... and adds the entries of its sketch
-    // row (in increasing tile row) into that row's accumulators, which no other
-    // thread touches during the tile.  Every sum has a fixed order (deterministic),
-    // and the count-sorted slots keep the lanes of a warp on equal trip counts.
-    if (do_sk) {
-      __syncthreads();  // y' of this tile complete
-      if (!MIXED) {
-        // per column: the largest exponent field of the tile, then the values in
-        // place as int64 fixed point (y' is not read again in a sketch pass)
-        for (int c = tid; c < b; c += NT) s_emax[c] = 0;
-        __syncthreads();
-        // (T a multiple of 32: the lanes of a warp share one column, so the warp takes
-        // its maximum first and one lane updates the shared value)
-        for (int t = tid; t < b * T; t += NT) {
-          const int c = t / T, r = t % T;
-          const unsigned long long u = (unsigned long long)__double_as_longlong(ys[(size_t)c * TP + r]);
-          int ex = r < rows ? (int)((u >> 52) & 0x7FF) : 0;
-          if ((T & 31) == 0) {
-            ex = __reduce_max_sync(0xffffffffu, ex);
-            if ((tid & 31) == 0 && ex != 0) atomicMax(&s_emax[c], ex);
-          } else if (ex != 0) {
-            atomicMax(&s_emax[c], ex);
-          }
-        }
-        __syncthreads();
-        for (int t = tid; t < b * T; t += NT) {
-          const int c = t / T, r = t % T;
-          const int E = s_emax[c];
-          const double yv = ys[(size_t)c * TP + r];
-          reinterpret_cast<long long*>(ys)[(size_t)c * TP + r] =
-              (r < rows && E != 0x7FF) ? fix_from_double(yv, E) : 0LL;
-        }
-        __syncthreads();
-      }
-      const uint32_t* meta = reinterpret_cast<const uint32_t*>(stage_R(s));
-      const uint8_t* lst = reinterpret_cast<const uint8_t*>(meta + rp.sk.mcap);
-      for (int q = tid; q < rp.sk.mcap; q += NT) {
-        const uint32_t m = meta[q];
-        if (m == 0xFFFFFFFFu) break;
-        const int i = (int)(m & 0xFFFu), o = (int)((m >> 12) & 0x7FFu), cnt = (int)(m >> 23);
-        const uint8_t* e = lst + o;
-        if (MIXED) {
-          for (int c0 = 0; c0 < b; c0 += CB) {
-            const int cw = min(CB, b - c0);
-            RBO_CW_DISPATCH(sketch_row_f32, cw, skf + i + (size_t)c0 * d, d,
-                            reinterpret_cast<const float*>(ys + (size_t)c0 * TP), 2 * TP, e, cnt)
-          }
-        } else {
-          for (int c0 = 0; c0 < b; c0 += CB) {
-            const int cw = min(CB, b - c0);
-            RBO_CW_DISPATCH(sketch_row_fix, cw, skd + i + (size_t)c0 * d, d,
-                            reinterpret_cast<const long long*>(ys) + (size_t)c0 * TP, TP, s_emax + c0,
-                            e, cnt)
           }
         }
       }
@@ -542,9 +406,6 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
       mypart[o] = sum;
     }
   }
-  if (do_sk) {
-    for (int t = tid; t < d * b; t += NT) mypart[P.no + t] = MIXED ? (double)skf[t] : skd[t];
-  }
   tree_reduce_epilogue(P, smem, &s_flag, &s_last);
 }
 
@@ -556,7 +417,7 @@ __global__ void __launch_bounds__(NT, (ARITH == 0 ? (SK ? 4 : 3) : 2)) rowpass_k
 constexpr int MAX_DEV = 64;
 static std::mutex g_launch_mu;
 static int g_num_sms[MAX_DEV] = {};
-static int g_smem_max[MAX_DEV][6] = {};
+static int g_smem_max[MAX_DEV][3] = {};
 static std::map<long long, int> g_occ;
 
 static int current_device() {
@@ -578,17 +439,17 @@ static int sm_count() {
 
 // Largest dynamic shared memory of the row-pass kernel (opt-in limit minus its
 // static shared memory); raises the kernel's limit to it on first use on a device.
-template <int ARITH, bool SK>
+template <int ARITH>
 static int smem_limit_locked(int dev) {
-  int& lim = g_smem_max[dev][ARITH * 2 + (SK ? 1 : 0)];
+  int& lim = g_smem_max[dev][ARITH];
   if (lim == 0) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     size_t stat = 0;
-    if (cudaFuncGetAttributes(&fa, rowpass_kernel<ARITH, SK>) == cudaSuccess) stat = fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, rowpass_kernel<ARITH>) == cudaSuccess) stat = fa.sharedSizeBytes;
     lim = optin - (int)stat - 64;
-    if (cudaFuncSetAttribute(rowpass_kernel<ARITH, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(rowpass_kernel<ARITH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              lim) != cudaSuccess) {
       cudaGetLastError();
       lim = 48 * 1024 - (int)stat;
@@ -597,23 +458,23 @@ static int smem_limit_locked(int dev) {
   return lim;
 }
 
-template <int ARITH, bool SK>
+template <int ARITH>
 static int smem_limit() {
   const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_launch_mu);
-  return smem_limit_locked<ARITH, SK>(dev);
+  return smem_limit_locked<ARITH>(dev);
 }
 
-template <int ARITH, bool SK>
+template <int ARITH>
 static int occupancy(int smem) {
   const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_launch_mu);
-  const long long key = ((long long)dev << 40) | ((long long)smem * 8 + ARITH * 2 + (SK ? 1 : 0));
+  const long long key = ((long long)dev << 40) | ((long long)smem * 4 + ARITH);
   auto it = g_occ.find(key);
   if (it != g_occ.end()) return it->second;
   int nb = 0;
-  smem_limit_locked<ARITH, SK>(dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<ARITH, SK>, NT, smem) !=
+  smem_limit_locked<ARITH>(dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rowpass_kernel<ARITH>, NT, smem) !=
       cudaSuccess) {
     cudaGetLastError();
     nb = 1;
@@ -621,24 +482,6 @@ static int occupancy(int smem) {
   if (nb < 1) nb = 1;
   g_occ[key] = nb;
   return nb;
-}
-
-// shared memory bytes of the small dense epilogue (beyond the reduced vector)
-static size_t epilogue_doubles(const RowPass& rp, int zr) {
-  const int b = rp.b, d = sketch_rows(rp);
-  const Epilogue& e = rp.epi;
-  size_t need = 0;
-  switch (e.op) {
-    case EPI_CHOL: need = (size_t)b * b * 2 + 64; break;
-    case EPI_HH: need = (size_t)d * b + (size_t)b * b + 2 * b + 64; break;
-    case EPI_SKB2: need = (size_t)3 * d * b + (size_t)2 * e.poff * b + (size_t)b * b + 2 * b + 64; break;
-    case EPI_GB: need = (size_t)(e.poff + b) * (e.poff + b) + 64; break;
-    case EPI_PIP: need = (size_t)b * b + 64; break;
-    case EPI_SKETCH_OUT: need = (size_t)d * b + 64; break;
-    default: break;
-  }
-  (void)zr;
-  return need;
 }
 
 int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launches) {
@@ -686,22 +529,18 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     if (rp.sk.rec == nullptr || rp.sk.mcap != sketch_sched_mcap(rp.sk.T, dsk, rp.sk_zeta) ||
         rp.sk.rec_bytes != sketch_sched_rec_bytes(rp.sk.T, dsk, rp.sk_zeta))
       return RBO_ERR_ARG;
+    return rowpass_sk_launch(rp, ar, st, launches, sm_count(), L, mixed);
   }
 
-  // tile height: the sketch schedule's with a sketch; otherwise the tallest tile up to
-  // 512 rows whose stage stays within STAGE_TARGET bytes (narrow panels need tall tiles
-  // to keep enough bytes in flight), at least 64 rows, halved while the layout does
-  // not fit
+  // tile height: the tallest tile up to 512 rows whose stage stays within STAGE_TARGET
+  // bytes (narrow panels need tall tiles to keep enough bytes in flight), at least 64
+  // rows, halved while the layout does not fit
   int T = 64;
-  if (dsk > 0) {
-    T = rp.sk.T;
-  } else {
-    while (T < 512 && (size_t)(rp.a + rp.b) * (2 * T + 2) * 8 <= STAGE_TARGET) T *= 2;
-  }
+  while (T < 512 && (size_t)(rp.a + rp.b) * (2 * T + 2) * 8 <= STAGE_TARGET) T *= 2;
   size_t smem = 0;
   int tpo = 1, tasks = 0;
-  size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_sk = 0,
-         rec_off = 0, off_red = 0, off_gth = 0;
+  size_t off_stage = 0, stage_bytes = 0, off_c = 0, off_tri = 0, off_dinv = 0, off_red = 0,
+         off_gth = 0;
   for (;;) {
     tpo = 1;
     if (items > 0)
@@ -709,34 +548,26 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
     tasks = items * tpo;
     const int TP = T + 2;
     off_stage = 64;
-    rec_off = (size_t)(rp.a + rp.b) * TP * 8;  // TP even: 16-byte multiple
-    stage_bytes = rec_off + (dsk > 0 ? (size_t)rp.sk.rec_bytes : 0);
+    stage_bytes = (size_t)(rp.a + rp.b) * TP * 8;  // TP even: 16-byte multiple
     size_t o = off_stage + NST * stage_bytes;
     off_c = o; o += (rp.C ? (size_t)rp.a * rp.b * 8 : 0);
     off_tri = o; o += (rp.Tri ? (size_t)rp.b * rp.b * 8 : 0);
     off_dinv = o; o += (rp.Tri ? (size_t)rp.b * 8 : 0);
     o = (o + 15) & ~size_t(15);
-    off_sk = o; o += (size_t)dsk * rp.b * (mixed ? 4 : 8);
-    o = (o + 15) & ~size_t(15);
     off_gth = o; o += (size_t)rp.sk_gd * TP * 8;
     size_t loop_bytes = o;
     size_t comb_bytes = off_stage + (size_t)tasks * CB * 8;
     off_red = 64;
-    size_t epi_bytes = off_red + ((size_t)L + 2) * 8 + epilogue_doubles(rp, zr) * 8;
+    size_t epi_bytes = off_red + ((size_t)L + 2) * 8 + epilogue_doubles(rp) * 8;
     smem = std::max(std::max(loop_bytes, epi_bytes), comb_bytes);
-    if (smem <= 220 * 1024 || T == 16 || dsk > 0) break;
+    if (smem <= 220 * 1024 || T == 16) break;
     T /= 2;
   }
-  const bool sk = dsk > 0;  // the scatter instance (no Gram: checked above)
-  const int limit = sk ? (arith == 1 ? smem_limit<1, true>() : smem_limit<0, true>())
-                       : (arith == 1 ? smem_limit<1, false>()
-                                     : (arith == 2 ? smem_limit<2, false>() : smem_limit<0, false>()));
+  const int limit = arith == 1 ? smem_limit<1>() : (arith == 2 ? smem_limit<2>() : smem_limit<0>());
   if ((long long)smem > limit) return RBO_ERR_ARG;
   const int ntiles = (int)((rp.n + T - 1) / T);
-  const int occ = sk ? (arith == 1 ? occupancy<1, true>((int)smem) : occupancy<0, true>((int)smem))
-                     : (arith == 1 ? occupancy<1, false>((int)smem)
-                                   : (arith == 2 ? occupancy<2, false>((int)smem)
-                                                 : occupancy<0, false>((int)smem)));
+  const int occ = arith == 1 ? occupancy<1>((int)smem)
+                             : (arith == 2 ? occupancy<2>((int)smem) : occupancy<0>((int)smem));
   int G = std::min(ntiles, occ * sm_count());
   if (rp.max_ctas > 0) G = std::min(G, rp.max_ctas);
   if (G < 1) G = 1;
@@ -768,9 +599,11 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   P.off_c = (int)off_c;
   P.off_tri = (int)off_tri;
   P.off_dinv = (int)off_dinv;
-  P.off_sk = (int)off_sk;
+  P.off_sk = 0;
   P.off_gth = (int)off_gth;
-  P.rec_off = (int)rec_off;
+  P.rec_off = 0;
+  P.off_ys = 0;
+  P.ystage_bytes = 0;
   P.off_red = (int)off_red;
   P.partials = nullptr;
   P.gpart = nullptr;
@@ -787,13 +620,11 @@ int rowpass_launch(const RowPass& rpin, Arena* ar, cudaStream_t st, int* launche
   }
   ProfToken tok = prof_start(st);
   if (arith == 1)
-    if (sk) rowpass_kernel<1, true><<<G, NT, smem, st>>>(P);
-    else rowpass_kernel<1, false><<<G, NT, smem, st>>>(P);
+    rowpass_kernel<1><<<G, NT, smem, st>>>(P);
   else if (arith == 2)
-    rowpass_kernel<2, false><<<G, NT, smem, st>>>(P);
+    rowpass_kernel<2><<<G, NT, smem, st>>>(P);
   else
-    if (sk) rowpass_kernel<0, true><<<G, NT, smem, st>>>(P);
-    else rowpass_kernel<0, false><<<G, NT, smem, st>>>(P);
+    rowpass_kernel<0><<<G, NT, smem, st>>>(P);
   if (prof_on()) {
     // algorithmic traffic: every n-row column read once, written once
     const double nn = (double)rp.n, A = rp.a, B = rp.b;
@@ -956,10 +787,7 @@ int rowpass_sketch_T(int a_max, int b_max, int d, int zeta) {
   // rows only while a stage stays within STAGE_TARGET
   for (int T = 128; T > 16; T /= 2) {
     if (T > 64 && (size_t)(a_max + b_max) * (T + 2) * 8 > STAGE_TARGET) continue;
-    size_t o = 64 + (size_t)NST * ((size_t)(a_max + b_max) * (T + 2) * 8 +
-                                   (size_t)sketch_sched_rec_bytes(T, d, zeta));
-    o += (size_t)a_max * b_max * 8 + 16 + (size_t)d * b_max * 8 + 16;
-    if (o <= 220 * 1024) return T;
+    if (rowpass_sk_loop_bytes(a_max, b_max, T, d, zeta) <= 220 * 1024) return T;
   }
   return 16;
 }

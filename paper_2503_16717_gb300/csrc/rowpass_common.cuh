@@ -38,6 +38,7 @@ struct PassDev {
   int off_stage, stage_bytes, off_c, off_tri, off_dinv, off_sk, off_red;
   int off_gth;            // Gaussian sketch entries of the tile (sk_gd x TP)
   int rec_off;            // sketch schedule record of the tile, offset inside a stage
+  int off_ys, ystage_bytes;  // sketch kernel: ring of Y stages (Y columns + record)
 };
 
 // ------------------------------------------------------------------------------------
@@ -378,5 +379,84 @@ __device__ __forceinline__ void tree_reduce_epilogue(const PassDev& P, unsigned 
   double* sm = red + ((P.L + 1) & ~1);
   run_epilogue(P, red, sm, s_flag);
 }
+
+// shared memory bytes of the small dense epilogue (beyond the reduced vector)
+static inline size_t epilogue_doubles(const RowPass& rp) {
+  const int b = rp.b, d = sketch_rows(rp);
+  const Epilogue& e = rp.epi;
+  size_t need = 0;
+  switch (e.op) {
+    case EPI_CHOL: need = (size_t)b * b * 2 + 64; break;
+    case EPI_HH: need = (size_t)d * b + (size_t)b * b + 2 * b + 64; break;
+    case EPI_SKB2: need = (size_t)3 * d * b + (size_t)2 * e.poff * b + (size_t)b * b + 2 * b + 64; break;
+    case EPI_GB: need = (size_t)(e.poff + b) * (e.poff + b) + 64; break;
+    case EPI_PIP: need = (size_t)b * b + 64; break;
+    case EPI_SKETCH_OUT: need = (size_t)d * b + 64; break;
+    default: break;
+  }
+  return need;
+}
+
+// ------------------------------------------------------------------------------------
+// sketch entry sums of one tile (both row-pass kernels)
+// ------------------------------------------------------------------------------------
+// Sketch of one sketch row over a tile, float64 path: the tile's values of each column
+// are held as int64 fixed point (unit 2^(E_c - 1077), E_c the column's largest
+// exponent field in the tile; fix_from_double); the row's entries are summed exactly
+// in integers (signs by integer negation), and the exact tile sum is rounded once to
+// float64 and added to the accumulator: one float64 add per (sketch row, column) and
+// tile instead of one per entry, on every lane.  A column with a non-finite value in
+// the tile (E_c = 0x7FF) makes the accumulators NaN.
+template <int CW>
+__device__ __forceinline__ void sketch_row_fix(double* acc, int d, const long long* y, int TP,
+                                               const int* emax, const uint8_t* e, int cnt) {
+  long long v[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) v[c] = 0;
+  for (int t = 0; t < cnt; ++t) {
+    const int ev = e[t];
+    const int r = ev >> 1;
+    const long long ng = -(long long)(ev & 1);  // 0 or all ones
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      const long long f = y[(size_t)c * TP + r];
+      v[c] += (f ^ ng) - ng;                     // f or -f
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CW; ++c) {
+    const double add = emax[c] == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
+                                        : double_from_fix(v[c], emax[c]);
+    acc[(size_t)c * d] += add;
+  }
+}
+// float32 values in the first 4 bytes of each 8-byte slot: y holds 2 floats per row
+template <int CW>
+__device__ __forceinline__ void sketch_row_f32(float* acc, int d, const float* y, int TP2,
+                                               const uint8_t* e, int cnt) {
+  float v[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) v[c] = acc[(size_t)c * d];
+  for (int t = 0; t < cnt; ++t) {
+    const int ev = e[t];
+    const int r = 2 * (ev >> 1);
+    const int sg = (ev & 1) << 31;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) v[c] += __int_as_float(__float_as_int(y[(size_t)c * TP2 + r]) ^ sg);
+  }
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[(size_t)c * d] = v[c];
+}
+#define RBO_CW_DISPATCH(fn, cw, ...)            \
+  switch (cw) {                                 \
+    case 8: fn<8>(__VA_ARGS__); break;          \
+    case 7: fn<7>(__VA_ARGS__); break;          \
+    case 6: fn<6>(__VA_ARGS__); break;          \
+    case 5: fn<5>(__VA_ARGS__); break;          \
+    case 4: fn<4>(__VA_ARGS__); break;          \
+    case 3: fn<3>(__VA_ARGS__); break;          \
+    case 2: fn<2>(__VA_ARGS__); break;          \
+    default: fn<1>(__VA_ARGS__); break;         \
+  }
 
 }  // namespace rbo
