@@ -305,17 +305,19 @@ def measured_traffic(passes, n, launches):
     of the two row-pass instances (profiles/rowpass_traffic.json): the Gram instance's
     DRAM/algorithmic ratio applied to the roles without a sketch, and for the update +
     sketch roles their algorithmic bytes plus the measured schedule-record bytes per row.
-    None when the row-pass source has changed since the counters were taken."""
+    None when a row-pass source has changed since the counters were taken."""
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
     try:
         with open(os.path.join(here, "profiles", "rowpass_traffic.json")) as f:
             rec = json.load(f)
-        with open(os.path.join(here, "paper_2503_16717_gb300", "csrc", "rowpass.cu"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = {}
+        for src in ("rowpass.cu", "rowpass_sk.cu"):
+            with open(os.path.join(here, "paper_2503_16717_gb300", "csrc", src), "rb") as f:
+                sha[src] = hashlib.sha256(f.read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if rec.get("rowpass_cu_sha256") != sha or not launches:
+    if rec.get("sources_sha256") != sha or not launches:
         return None
     ratio = rec["instances"]["gram"]["ratio"]
     per_row = rec["instances"]["update_sketch"]["schedule_record_bytes_per_row"]
