@@ -254,6 +254,7 @@ static __device__ void run_epilogue(const PassDev& P, const double* red, double*
       double* beta = R + k * k;
       double* sg = beta + k;
       double* scr = sg + k;
+      if (pp > 0) cta_prefetch_cols(e.qs, d, d, pp);
       load_sketch(P, red, v);
       if (pp > 0) {
         cta_gemm_tn(e.qs, d, v, d, pp, k, c1);
