@@ -669,6 +669,43 @@ def run_learned(rbo, torch, args):
             "infer_gbs_algorithmic": bytes_infer / (infer_ms / 1e3) / 1e9 if infer_ms else None}
 
 
+def run_gnn_kernels(rbo, torch):
+    """Kernel times of the learned-SPAI network alone (--gnn-only): one inference on an
+    unseen 2048^2 convection-diffusion instance (n = 4.19M, 21M edges) and one loss and
+    gradient on a 512^2 training instance with 8 residual columns, each timed with CUDA
+    events over 5 calls after a warm-up call.  Weights: the initial ones plus seeded
+    N(0, 0.05^2) noise (the cost does not depend on their values)."""
+    import numpy as np
+    import synth
+    net = rbo.GNN(seed=2)
+    rng = np.random.default_rng(1)
+    th = net.get_params()
+    net.set_params((th + rng.standard_normal(th.shape) * 0.05).astype(np.float32))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    Ah, _ = synth.convdiff2d_csr(2048, 4000)
+    A = rbo.DeviceCSR.from_host(Ah)
+    infer_ms = timed(lambda: net.infer(A))
+    Bh, _ = synth.convdiff2d_csr(512, 3000)
+    B = rbo.DeviceCSR.from_host(Bh)
+    R = rbo.colmajor(Bh.n, 8)
+    R.copy_(torch.from_numpy(np.random.default_rng(2).standard_normal((Bh.n, 8))))
+    grad_ms = timed(lambda: net.loss_grad(B, R))
+    return {"infer_ms": infer_ms, "infer_n": int(A.n), "infer_edges": int(A.nnz),
+            "loss_grad_ms": grad_ms, "loss_grad_n": int(B.n), "loss_grad_edges": int(B.nnz),
+            "residual_columns": 8}
+
+
 def run_s_sweep(rbo, torch, Ad, bd, args):
     """Time to solution of the benchmark problem against the block size s (Sec. 8:
     sketching keeps larger s stable): one-stage and two-stage (s_hat = the smallest
@@ -928,7 +965,15 @@ def main():
                          "bases at s = 10, 20, 25")
     ap.add_argument("--s-sweep", action="store_true",
                     help="also time the workload's solves for s in 5, 10, 15, 20, 30")
+    ap.add_argument("--gnn-only", action="store_true",
+                    help="only time the learned-SPAI network's inference (2048^2) and loss and "
+                         "gradient (512^2), print them as one JSON object and exit")
     args = ap.parse_args()
+    if args.gnn_only:
+        import torch
+        import paper_2503_16717_gb300 as rbo
+        print(json.dumps({"gnn_kernels": run_gnn_kernels(rbo, torch)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -13,8 +13,10 @@
 //   M_ij = (wo . [e_ij; h_i; h_j] + bo + [i == j]) / A_ii
 // Loss over residual columns r_k: mean_k ||r_k - A M r_k||^2 / ||r_k||^2.
 //
-// One warp handles one node or edge with lane = channel (width 32 = warp size);
-// matrix-vector products broadcast the input channels with shuffles.  Every sum
+// The message and node-update layers of the forward pass run on the tensor cores
+// (gnn_tc.cu).  The other kernels here give one warp to one node or edge with lane =
+// channel (width 32 = warp size); their matrix-vector products broadcast the input
+// channels with shuffles.  Every sum
 // over edges or nodes runs in a fixed order (rows in CSR order, per-block partials
 // reduced in block order), so results are reproducible.  The pattern of A must be
 // structurally symmetric (the transpose of edge (i, j) is located by binary search
@@ -27,21 +29,10 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "gnn_params.cuh"
 
 namespace rbo {
 namespace gnn {
-
-constexpr int W = 32;
-constexpr int NL = 3;
-constexpr int OFF_WN = 0, OFF_BN = 64, OFF_WE = 96, OFF_BE = 192, OFF_L0 = 224;
-constexpr int LAYER_SZ = 2048 + 32 + 2048 + 32;
-constexpr int OFF_WO = OFF_L0 + NL * LAYER_SZ;  // 12704
-constexpr int OFF_BO = OFF_WO + 96;
-constexpr int NPARAM = OFF_BO + 1;               // 12801
-__host__ __device__ constexpr int off_wm(int l) { return OFF_L0 + l * LAYER_SZ; }
-__host__ __device__ constexpr int off_bm(int l) { return off_wm(l) + 2048; }
-__host__ __device__ constexpr int off_wh(int l) { return off_wm(l) + 2080; }
-__host__ __device__ constexpr int off_bh(int l) { return off_wm(l) + 4128; }
 
 __device__ __forceinline__ float bf(const __nv_bfloat16* w, int i) { return __bfloat162float(w[i]); }
 __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
@@ -110,63 +101,6 @@ __global__ void encode_kernel(int64_t cnt, int nin, const float* __restrict__ in
   float z = bf(w, off_b + c);
   for (int k = 0; k < nin; ++k) z = fmaf(bf(w, off_w + c * nin + k), in[it * nin + k], z);
   out[t] = relu(z);
-}
-
-// message layer: warp per edge, lane = output channel
-__global__ void message_kernel(int64_t nnz, const int32_t* __restrict__ col,
-                               const float* __restrict__ ein, const float* __restrict__ h,
-                               const __nv_bfloat16* __restrict__ w, int l, float* __restrict__ m,
-                               float* __restrict__ eout) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float wr[2 * W];
-#pragma unroll
-  for (int k = 0; k < 2 * W; ++k) wr[k] = bf(w, off_wm(l) + lane * 2 * W + k);
-  const float bias = bf(w, off_bm(l) + lane);
-  for (int64_t e = warp0; e < nnz; e += nwarps) {
-    const float ev = ein[e * W + lane];
-    const float hv = h[(int64_t)col[e] * W + lane];
-    float z = bias;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      z = fmaf(wr[k], __shfl_sync(0xffffffffu, ev, k), z);
-      z = fmaf(wr[W + k], __shfl_sync(0xffffffffu, hv, k), z);
-    }
-    const float mv = relu(z);
-    m[e * W + lane] = mv;
-    eout[e * W + lane] = ev + mv;
-  }
-}
-
-// aggregation + node update: warp per node
-__global__ void node_update_kernel(int64_t n, const int32_t* __restrict__ rowptr,
-                                   const float* __restrict__ m, const float* __restrict__ hin,
-                                   const __nv_bfloat16* __restrict__ w, int l,
-                                   float* __restrict__ agg, float* __restrict__ rh,
-                                   float* __restrict__ hout) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float wr[2 * W];
-#pragma unroll
-  for (int k = 0; k < 2 * W; ++k) wr[k] = bf(w, off_wh(l) + lane * 2 * W + k);
-  const float bias = bf(w, off_bh(l) + lane);
-  for (int64_t i = warp0; i < n; i += nwarps) {
-    float a = 0.f;
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) a += m[(int64_t)e * W + lane];
-    const float hv = hin[i * W + lane];
-    float z = bias;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      z = fmaf(wr[k], __shfl_sync(0xffffffffu, hv, k), z);
-      z = fmaf(wr[W + k], __shfl_sync(0xffffffffu, a, k), z);
-    }
-    const float r = relu(z);
-    agg[i * W + lane] = a;
-    rh[i * W + lane] = r;
-    hout[i * W + lane] = hv + r;
-  }
 }
 
 // decoder: M_e = (wo . [e; h_i; h_j] + bo + [i == j]) / A_ii, warp per edge

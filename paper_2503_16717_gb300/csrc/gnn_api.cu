@@ -9,22 +9,11 @@
 #include <cstring>
 #include <vector>
 
+#include "gnn_params.cuh"
 #include "rbo_internal.cuh"
 
 namespace rbo {
 namespace gnn {
-
-constexpr int W = 32;
-constexpr int NL = 3;
-constexpr int OFF_WN = 0, OFF_BN = 64, OFF_WE = 96, OFF_BE = 192, OFF_L0 = 224;
-constexpr int LAYER_SZ = 2048 + 32 + 2048 + 32;
-constexpr int OFF_WO = OFF_L0 + NL * LAYER_SZ;
-constexpr int OFF_BO = OFF_WO + 96;
-constexpr int NPARAM = OFF_BO + 1;
-constexpr int off_wm(int l) { return OFF_L0 + l * LAYER_SZ; }
-constexpr int off_bm(int l) { return off_wm(l) + 2048; }
-constexpr int off_wh(int l) { return off_wm(l) + 2080; }
-constexpr int off_bh(int l) { return off_wm(l) + 4128; }
 
 // kernels (gnn.cu)
 __global__ void graph_edges_kernel(int64_t, const int32_t*, const int32_t*, const double*, int32_t*,
@@ -32,10 +21,13 @@ __global__ void graph_edges_kernel(int64_t, const int32_t*, const int32_t*, cons
 __global__ void graph_features_kernel(int64_t, const int32_t*, const int32_t*, const double*,
                                       const int32_t*, const double*, float*, float*);
 __global__ void encode_kernel(int64_t, int, const float*, const __nv_bfloat16*, int, int, float*);
-__global__ void message_kernel(int64_t, const int32_t*, const float*, const float*,
-                               const __nv_bfloat16*, int, float*, float*);
-__global__ void node_update_kernel(int64_t, const int32_t*, const float*, const float*,
-                                   const __nv_bfloat16*, int, float*, float*, float*);
+// tensor-core message and node-update layers (gnn_tc.cu)
+int message_tc_launch(int64_t nnz, int64_t n, const int32_t* col, const float* ein, const float* h,
+                      const __nv_bfloat16* w, int l, float* m, float* eout, DevStatus* status,
+                      cudaStream_t st);
+int node_update_tc_launch(int64_t n, const int32_t* rowptr, const float* m, const float* hin,
+                          const __nv_bfloat16* w, int l, float* agg, float* rh, float* hout,
+                          DevStatus* status, cudaStream_t st);
 __global__ void decode_kernel(int64_t, const int32_t*, const int32_t*, const float*, const float*,
                               const __nv_bfloat16*, const double*, double*);
 __global__ void spmm_kernel(int64_t, int, const int32_t*, const int32_t*, const double*,
@@ -276,8 +268,10 @@ static int forward(rbo_gnn_s* g, const rbo_csr* A, Work& w, Arena* ar, cudaStrea
     float* mm = train ? w.m[l] : w.m[0];
     float* ag = train ? w.agg[l] : w.agg[0];
     float* rr = train ? w.rh[l] : w.rh[0];
-    message_kernel<<<gridw(nnz), 256, 0, st>>>(nnz, A->col, w.e[a], w.h[a], g->wbf, l, mm, w.e[b]);
-    node_update_kernel<<<gridw(n), 256, 0, st>>>(n, A->rowptr, mm, w.h[a], g->wbf, l, ag, rr, w.h[b]);
+    int rc = message_tc_launch(nnz, n, A->col, w.e[a], w.h[a], g->wbf, l, mm, w.e[b], ar->status, st);
+    if (rc == RBO_OK)
+      rc = node_update_tc_launch(n, A->rowptr, mm, w.h[a], g->wbf, l, ag, rr, w.h[b], ar->status, st);
+    if (rc != RBO_OK) return rc;
     *launches += 2;
   }
   const int last = train ? NL : (NL & 1);
