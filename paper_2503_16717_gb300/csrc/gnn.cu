@@ -13,7 +13,7 @@
 //   M_ij = (wo . [e_ij; h_i; h_j] + bo + [i == j]) / A_ii
 // Loss over residual columns r_k: mean_k ||r_k - A M r_k||^2 / ||r_k||^2.
 //
-// The message and node-update layers of the forward pass run on the tensor cores
+// The message and node-update layers and their backward run on the tensor cores
 // (gnn_tc.cu).  The other kernels here give one warp to one node or edge with lane =
 // channel (width 32 = warp size); their matrix-vector products broadcast the input
 // channels with shuffles.  Every sum
@@ -264,100 +264,6 @@ __global__ void decode_back_nodes_kernel(int64_t n, const int32_t* __restrict__ 
     s2 += dout[tpos[e]];
   }
   dh[t] = bf(w, OFF_WO + W + c) * s1 + bf(w, OFF_WO + 2 * W + c) * s2;
-}
-
-// node update backward (layer l): warp per node.
-//   dzh = dh * [rh > 0];  g_Wh += dzh v^T (v = [h_l, agg_l]);  g_bh += dzh
-//   dv = Wh^T dzh;  dh_l = dh + dv[:32];  dagg = dv[32:]
-__global__ void node_back_kernel(int64_t n, const float* __restrict__ dh, const float* __restrict__ rh,
-                                 const float* __restrict__ hin, const float* __restrict__ agg,
-                                 const __nv_bfloat16* __restrict__ w, int l, float* __restrict__ dhl,
-                                 float* __restrict__ dagg, float* __restrict__ part) {
-  extern __shared__ float sred[];
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // column `lane` and `32 + lane` of Wh (rows c = 0..31)
-  float wc[2 * W];
-#pragma unroll
-  for (int c = 0; c < W; ++c) {
-    wc[c] = bf(w, off_wh(l) + c * 2 * W + lane);
-    wc[W + c] = bf(w, off_wh(l) + c * 2 * W + W + lane);
-  }
-  float g[2 * W + 1];
-#pragma unroll
-  for (int k = 0; k < 2 * W + 1; ++k) g[k] = 0.f;
-  for (int64_t i = warp0; i < n; i += nwarps) {
-    const float dz = rh[i * W + lane] > 0.f ? dh[i * W + lane] : 0.f;
-    const float hv = hin[i * W + lane], av = agg[i * W + lane];
-    float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      // g_Wh[lane][k] += dz * v[k],  v[k] = h[k], v[32+k] = agg[k]
-      const float hk = __shfl_sync(0xffffffffu, hv, k);
-      const float ak = __shfl_sync(0xffffffffu, av, k);
-      g[k] = fmaf(dz, hk, g[k]);
-      g[W + k] = fmaf(dz, ak, g[W + k]);
-      // dv[lane] = sum_c Wh[c][lane] dz_c
-      const float dzc = __shfl_sync(0xffffffffu, dz, k);
-      d0 = fmaf(wc[k], dzc, d0);
-      d1 = fmaf(wc[W + k], dzc, d1);
-    }
-    g[2 * W] += dz;
-    dhl[i * W + lane] = dh[i * W + lane] + d0;
-    dagg[i * W + lane] = d1;
-  }
-  // g holds row `lane` of the weight gradient (64 values) and the bias gradient;
-  // element (lane, k) of the partial sits at k * 32 + lane
-  block_partial_store(g, (2 * W + 1) * 32, sred, part);
-}
-
-// message backward (layer l): warp per edge.
-//   dm = de + dagg[i];  dzm = dm * [m > 0];  g_Wm += dzm u^T (u = [e_l, h_l[j]]);  g_bm += dzm
-//   du = Wm^T dzm;  de_l = de + du[:32];  dhj[e] = du[32:]  (gathered per node later)
-__global__ void message_back_kernel(int64_t nnz, const int32_t* __restrict__ erow,
-                                    const int32_t* __restrict__ col, const float* __restrict__ de,
-                                    const float* __restrict__ dagg, const float* __restrict__ m,
-                                    const float* __restrict__ ein, const float* __restrict__ h,
-                                    const __nv_bfloat16* __restrict__ w, int l,
-                                    float* __restrict__ del, float* __restrict__ dhj,
-                                    float* __restrict__ part) {
-  extern __shared__ float sred[];
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float wc[2 * W];
-#pragma unroll
-  for (int c = 0; c < W; ++c) {
-    wc[c] = bf(w, off_wm(l) + c * 2 * W + lane);
-    wc[W + c] = bf(w, off_wm(l) + c * 2 * W + W + lane);
-  }
-  float g[2 * W + 1];
-#pragma unroll
-  for (int k = 0; k < 2 * W + 1; ++k) g[k] = 0.f;
-  for (int64_t q = warp0; q < nnz; q += nwarps) {
-    const int i = erow[q], j = col[q];
-    const float dmv = de[q * W + lane] + dagg[(int64_t)i * W + lane];
-    const float dz = m[q * W + lane] > 0.f ? dmv : 0.f;
-    const float ev = ein[q * W + lane], hv = h[(int64_t)j * W + lane];
-    float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      const float ek = __shfl_sync(0xffffffffu, ev, k);
-      const float hk = __shfl_sync(0xffffffffu, hv, k);
-      g[k] = fmaf(dz, ek, g[k]);
-      g[W + k] = fmaf(dz, hk, g[W + k]);
-      const float dzc = __shfl_sync(0xffffffffu, dz, k);
-      d0 = fmaf(wc[k], dzc, d0);
-      d1 = fmaf(wc[W + k], dzc, d1);
-    }
-    g[2 * W] += dz;
-    del[q * W + lane] = de[q * W + lane] + d0;
-    dhj[q * W + lane] = d1;
-  }
-  // g holds row `lane` of the weight gradient (64 values) and the bias gradient;
-  // element (lane, k) of the partial sits at k * 32 + lane
-  block_partial_store(g, (2 * W + 1) * 32, sred, part);
 }
 
 // dh_l[i] += sum over row i of dhj[tpos e]  (the column scatter, gathered per node)

@@ -44,11 +44,11 @@ __global__ void decode_back_edges_kernel(int64_t, const int32_t*, const int32_t*
                                          float*);
 __global__ void decode_back_nodes_kernel(int64_t, const int32_t*, const int32_t*, const float*,
                                          const __nv_bfloat16*, float*);
-__global__ void node_back_kernel(int64_t, const float*, const float*, const float*, const float*,
-                                 const __nv_bfloat16*, int, float*, float*, float*);
-__global__ void message_back_kernel(int64_t, const int32_t*, const int32_t*, const float*,
-                                    const float*, const float*, const float*, const float*,
-                                    const __nv_bfloat16*, int, float*, float*, float*);
+int layer_back_tc_launch(bool msg, int64_t cnt, int64_t n, const int32_t* erow, const int32_t* col,
+                         const float* g, const float* dagg, const float* act, const float* u0,
+                         const float* u1, const __nv_bfloat16* w, int off_w, float* out0, float* out1,
+                         float* part, int max_blocks, DevStatus* status, cudaStream_t st,
+                         int* nblocks);
 __global__ void gather_cols_kernel(int64_t, const int32_t*, const int32_t*, const float*, float*);
 __global__ void encode_back_kernel(int64_t, int, const float*, const float*, const float*, float*);
 __global__ void reduce_partials_kernel(const float*, int, int, const int*, const int*, int, float*);
@@ -281,8 +281,9 @@ static int forward(rbo_gnn_s* g, const rbo_csr* A, Work& w, Arena* ar, cudaStrea
   return note_cuda(cudaGetLastError());
 }
 
-static void reduce_group(const Map& m, const float* part, float* grad, cudaStream_t st) {
-  reduce_partials_kernel<<<grid1(m.nmap), 256, 0, st>>>(part, NBLK_RED, m.cnt, m.src, m.dst, m.nmap,
+static void reduce_group(const Map& m, const float* part, float* grad, cudaStream_t st,
+                         int nblocks = NBLK_RED) {
+  reduce_partials_kernel<<<grid1(m.nmap), 256, 0, st>>>(part, nblocks, m.cnt, m.src, m.dst, m.nmap,
                                                         grad);
 }
 
@@ -329,7 +330,7 @@ static int loss_grad(rbo_gnn_s* g, const rbo_csr* A, const double* R, int nr, in
   dm_kernel<<<grid1(nnz), 256, 0, st>>>(nnz, nr, w.erow, A->col, w.dZ, n, R, ldr, w.dinv, w.dout);
   *launches += 3;
   // decoder
-  const size_t sm_dec = (size_t)(BLK / 32) * 128 * 4, sm_l = (size_t)(BLK / 32) * 65 * 32 * 4,
+  const size_t sm_dec = (size_t)(BLK / 32) * 128 * 4,
                sm_enc = (size_t)(BLK / 32) * 32 * 32 * 4;
   decode_back_edges_kernel<<<NBLK_RED, BLK, sm_dec, st>>>(nnz, w.erow, A->col, w.e[NL], w.h[NL],
                                                           w.dout, g->wbf, w.de, w.part);
@@ -338,12 +339,17 @@ static int loss_grad(rbo_gnn_s* g, const rbo_csr* A, const double* R, int nr, in
   *launches += 3;
   float *dh = w.dh, *dhn = w.dh2, *de = w.de, *den = w.de2;
   for (int l = NL - 1; l >= 0; --l) {
-    node_back_kernel<<<NBLK_RED, BLK, sm_l, st>>>(n, dh, w.rh[l], w.h[l], w.agg[l], g->wbf, l, dhn,
-                                                  w.dagg, w.part);
-    reduce_group(g->layer_node[l], w.part, g->grad, st);
-    message_back_kernel<<<NBLK_RED, BLK, sm_l, st>>>(nnz, w.erow, A->col, de, w.dagg, w.m[l], w.e[l],
-                                                     w.h[l], g->wbf, l, den, w.dhj, w.part);
-    reduce_group(g->layer_msg[l], w.part, g->grad, st);
+    int nb = 0;
+    if ((e = layer_back_tc_launch(false, n, n, nullptr, nullptr, dh, nullptr, w.rh[l], w.h[l],
+                                  w.agg[l], g->wbf, off_wh(l), dhn, w.dagg, w.part, NBLK_RED,
+                                  ar->status, st, &nb)))
+      return e;
+    reduce_group(g->layer_node[l], w.part, g->grad, st, nb);
+    if ((e = layer_back_tc_launch(true, nnz, n, w.erow, A->col, de, w.dagg, w.m[l], w.e[l], w.h[l],
+                                  g->wbf, off_wm(l), den, w.dhj, w.part, NBLK_RED, ar->status, st,
+                                  &nb)))
+      return e;
+    reduce_group(g->layer_msg[l], w.part, g->grad, st, nb);
     gather_cols_kernel<<<grid1(n * W), 256, 0, st>>>(n, A->rowptr, w.tpos, w.dhj, dhn);
     *launches += 5;
     std::swap(dh, dhn);

@@ -90,6 +90,18 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+// 32 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+      "%29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+      "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+      "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // 32 consecutive 32-bit columns of this thread's lane; the wait is in the same statement
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -365,6 +377,278 @@ __global__ void __launch_bounds__(TNT, TCTAS)
   tc_teardown(&s_fin, tbase);
 }
 
+// ---- backward of the message and node-update layers ------------------------------------
+// Per item (edge q = (i, j) for the message layer, node i for the node update), with
+// u = the layer's 64 inputs and a = its output after the ReLU:
+//   dz = g * [a > 0]   (g = de_q + dagg_i for a message, dh_i for a node update)
+//   dW += dz u^T,  db += dz,  du = W^T dz
+//   outputs: g + du[0:32] (gradient of e_q or h_i), du[32:64] (of h_j per edge, or agg_i)
+// Both contractions run on the tensor cores, per tile of 128 items:
+//   du (M = 128 items, N = 64, K = 32): A = dz split into three bfloat16 pieces (tensor
+//     memory, row = item), B = W^T (shared memory);
+//   dW^T (M = 128 = (piece p of u, input k), N = 64 = (piece q of dz, output c), K = the
+//     tile's items): A = the hi (p = 0) and lo (p = 1) bfloat16 pieces of u, row (p, k),
+//     two items per 32-bit column; B = the hi and lo pieces of dz (shared memory, K = item);
+//     accumulated in tensor memory over all tiles of the CTA.  The four piece products sum
+//     to u dz^T within about 2^-16 relative per term.
+// At the end each CTA writes its partial of dW (element (c, k) at k * 32 + c) and db
+// (at 64 * 32 + c), summed over the CTAs in a fixed order by the reduction kernel.
+struct BackArgs {
+  int64_t cnt;               // items: edges or nodes
+  int64_t n;                 // nodes (bound of the gathered indices)
+  const int32_t* erow;       // message: row i of edge q
+  const int32_t* col;        // message: column j of edge q
+  const float* g;            // gradient reaching the item's output (de or dh), per item
+  const float* dagg;         // message: gradient of each node's aggregate, added to de
+  const float* act;          // the layer's output after the ReLU (m or rh), per item
+  const float* u0;           // inputs 0..31 (e_l per edge, h_l per node), per item
+  const float* u1;           // inputs 32..63 (h_l[j] gathered per edge, agg_l per node)
+  const __nv_bfloat16* w;    // bfloat16 parameters
+  int off_w;                 // the layer's 32 x 64 weight matrix
+  float* out0;               // g + du[0:32]
+  float* out1;               // du[32:64]
+  float* part;               // per-CTA partials, 65 * 32 floats each
+  DevStatus* status;
+};
+
+constexpr int BLD = 97;                         // buffer row: dz (32) | u (64), + 1
+constexpr int BOFF_BDU = 49 * 1024;             // after 4 x 32 x 97 floats (49664 bytes)
+constexpr int BOFF_BG = BOFF_BDU + 4096;        // B of du: 2 K-steps x 64 rows x 32 bytes
+constexpr int BSMEM_USED = BOFF_BG + 16384;     // B of dW: 8 K-steps x 64 rows x 32 bytes
+// dynamic shared memory per CTA: enough padding that at most two CTAs fit on an SM (each
+// holds half of the tensor memory)
+constexpr int BSMEM = 80 * 1024;
+constexpr uint32_t BCOLS = 256;                 // tensor memory: A_du, D_du, A_dW, D_dW
+constexpr uint32_t B_ADU = 0, B_DDU = 64, B_AG = 128, B_DG = 192;
+static_assert(4 * 32 * BLD * 4 <= BOFF_BDU, "backward buffers overlap B");
+static_assert(BSMEM_USED + 1024 <= BSMEM, "tensor-core GNN backward exceeds its shared memory");
+
+template <bool MSG>
+__global__ void __launch_bounds__(TNT, 2) layer_back_tc_kernel(const __grid_constant__ BackArgs P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mma, s_fin;
+  __shared__ int s_skip;
+  __shared__ float s_db[4][32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_skip = read_code(P.status) != 0;
+  __syncthreads();
+  if (s_skip) return;
+  unsigned char* smem = align1k(smem_raw);
+  float* bufs = reinterpret_cast<float*>(smem);
+  float* buf = bufs + warp * 32 * BLD;
+  unsigned char* Bdu = smem + BOFF_BDU;
+  unsigned char* Bg = smem + BOFF_BG;
+  // B of du = W^T: row n = input k, K index = output c (W[c][k] at w + off_w + 64 c + k)
+  for (int t = tid; t < 32 * 64; t += TNT) {
+    const int c = t >> 6, k = t & 63;
+    const int o = (c >> 4) * 2048 + (k >> 3) * 256 + ((c >> 3) & 1) * 128 + (k & 7) * 16 + (c & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(Bdu + o) = P.w[P.off_w + t];
+  }
+  fence_proxy_async();
+  if (tid == 0) {
+    mbar_init(&s_mma, 1);
+    mbar_init(&s_fin, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(BCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tb = s_tmem;
+  const uint32_t tl = tb + ((uint32_t)(warp * 32) << 16);
+  // this thread's row of the dW^T product: piece gp of input gk
+  const int gk = 32 * (warp & 1) + lane, gp = warp >> 1;
+  float db = 0.f;
+  const int64_t ntiles = (P.cnt + TT - 1) / TT;
+  bool bad = false, ok = true;
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int64_t q0 = tile * TT + warp * 32;
+    int ri = -1, cj = -1;
+    if (MSG && q0 + lane < P.cnt) {
+      ri = P.erow[q0 + lane];
+      cj = P.col[q0 + lane];
+      if (ri < 0 || (int64_t)ri >= P.n || cj < 0 || (int64_t)cj >= P.n) {
+        bad = true;
+        ri = cj = -1;
+      }
+    }
+    float r[32];
+    __syncwarp();  // the previous tile's reads of the buffer are done
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float dz[16];
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = 16 * half + jj;
+        const int64_t q = q0 + j;
+        float gv = 0.f, av = 0.f, x0 = 0.f, x1 = 0.f;
+        if (MSG) {
+          const int i = __shfl_sync(0xffffffffu, ri, j);
+          const int c = __shfl_sync(0xffffffffu, cj, j);
+          if (q < P.cnt && i >= 0) {
+            gv = P.g[q * W + lane];
+            av = P.act[q * W + lane];
+            x0 = P.u0[q * W + lane];
+            x1 = P.u1[(int64_t)c * W + lane];
+            r[j] = gv;
+            gv += P.dagg[(int64_t)i * W + lane];
+          } else {
+            r[j] = 0.f;
+          }
+        } else {
+          if (q < P.cnt) {
+            gv = P.g[q * W + lane];
+            av = P.act[q * W + lane];
+            x0 = P.u0[q * W + lane];
+            x1 = P.u1[q * W + lane];
+          }
+          r[j] = gv;
+        }
+        dz[jj] = av > 0.f ? gv : 0.f;
+        buf[j * BLD + lane] = dz[jj];
+        buf[j * BLD + 32 + lane] = x0;
+        buf[j * BLD + 64 + lane] = x1;
+        db += dz[jj];
+      }
+      // B of dW: row 32 q + c (piece q of dz_c), K = item; two items per 32-bit word
+#pragma unroll
+      for (int jj = 0; jj < 16; jj += 2) {
+        const int item = warp * 32 + 16 * half + jj;
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(dz[jj], dz[jj + 1]);
+        const float2 hf = __bfloat1622float2(hi);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(dz[jj] - hf.x, dz[jj + 1] - hf.y);
+        const int ob = (item >> 4) * 2048 + ((item >> 3) & 1) * 128 + (item & 7) * 2;
+        const int r1 = 32 + lane;
+        *reinterpret_cast<__nv_bfloat162*>(Bg + ob + (lane >> 3) * 256 + (lane & 7) * 16) = hi;
+        *reinterpret_cast<__nv_bfloat162*>(Bg + ob + (r1 >> 3) * 256 + (r1 & 7) * 16) = lo;
+      }
+    }
+    fence_proxy_async();  // B of dW written through the generic proxy
+    __syncwarp();
+    {  // A of du: this thread's item, dz in three pieces (K = 32: 16 columns each)
+      float x[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) x[k] = buf[lane * BLD + k];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        uint32_t wd[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const __nv_bfloat162 b = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+          const float2 f = __bfloat1622float2(b);
+          x[2 * j] -= f.x;
+          x[2 * j + 1] -= f.y;
+          wd[j] = *reinterpret_cast<const uint32_t*>(&b);
+        }
+        tmem_st16(tl + B_ADU + (uint32_t)(16 * p), wd);
+      }
+    }
+    __syncthreads();  // every warp's rows are in the buffers
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {  // A of dW: input gk of the tile's items, piece gp
+      uint32_t wd[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int item = 64 * h2 + 2 * c;
+        const float* rowp = bufs + (item >> 5) * 32 * BLD + (item & 31) * BLD + 32 + gk;
+        const float v0 = rowp[0], v1 = rowp[BLD];
+        __nv_bfloat162 b = __floats2bfloat162_rn(v0, v1);
+        if (gp) {
+          const float2 f = __bfloat1622float2(b);
+          b = __floats2bfloat162_rn(v0 - f.x, v1 - f.y);
+        }
+        wd[c] = *reinterpret_cast<const uint32_t*>(&b);
+      }
+      tmem_st32(tl + B_AG + (uint32_t)(32 * h2), wd);
+    }
+    tmem_st_wait();
+    tc_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_after();
+      const uint32_t id = idesc_bf16(TT, 64);
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          mma_bf16(tb + B_DDU, tb + B_ADU + (uint32_t)(16 * p + 8 * ks),
+                   desc_nosw(smem_u32(Bdu + ks * 2048), 128, 256), id, (p | ks) != 0 ? 1u : 0u);
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks)
+        mma_bf16(tb + B_DG, tb + B_AG + (uint32_t)(8 * ks), desc_nosw(smem_u32(Bg + ks * 2048), 128, 256),
+                 id, (it > 0 || ks > 0) ? 1u : 0u);
+      mma_commit_to(&s_mma);
+    }
+    const bool done = mbar_wait_bounded(&s_mma, (uint32_t)(it & 1));
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) set_error(P.status, RBO_ERR_TIMEOUT, 43);
+      ok = false;
+      break;
+    }
+    tc_after();
+    {  // du rows into buffer columns 32..95 (u is no longer read)
+      uint32_t z[32];
+      tmem_ld32(tl + B_DDU, z);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) buf[lane * BLD + 32 + c] = __uint_as_float(z[c]);
+      tmem_ld32(tl + B_DDU + 32, z);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) buf[lane * BLD + 64 + c] = __uint_as_float(z[c]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (q0 + j < P.cnt) {
+        P.out0[(q0 + j) * W + lane] = r[j] + buf[j * BLD + 32 + lane];
+        P.out1[(q0 + j) * W + lane] = buf[j * BLD + 64 + lane];
+      }
+    }
+  }
+  if (MSG && __any_sync(0xffffffffu, bad) && lane == 0) set_error(P.status, RBO_ERR_ARG, 44);
+  if (ok) {
+    // this thread's dW^T row summed over the pieces of dz; the hi and lo pieces of u sit
+    // in warps (0, 1) and (2, 3)
+    uint32_t z0[32], z1[32];
+    tmem_ld32(tl + B_DG, z0);
+    tmem_ld32(tl + B_DG + 32, z1);
+    float sg[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) sg[c] = __uint_as_float(z0[c]) + __uint_as_float(z1[c]);
+    __syncthreads();  // every buffer read of the last tile is done
+    float* sc = bufs;  // 64 x 33 floats
+    if (gp == 1) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) sc[gk * 33 + c] = sg[c];
+    }
+    s_db[warp][lane] = db;
+    __syncthreads();
+    float* part = P.part + (int64_t)blockIdx.x * (65 * 32);
+    if (gp == 0) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) part[gk * 32 + c] = sg[c] + sc[gk * 33 + c];
+    }
+    if (warp == 0) part[64 * 32 + lane] = s_db[0][lane] + s_db[1][lane] + s_db[2][lane] + s_db[3][lane];
+  }
+  // every product issued has completed before the tensor memory is freed
+  if (tid == 0) {
+    mma_commit_to(&s_fin);
+    mbar_wait_bounded(&s_fin, 0u);
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb), "r"(BCOLS));
+  }
+}
+
 static int tc_grid(int64_t items) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -387,6 +671,35 @@ int node_update_tc_launch(int64_t n, const int32_t* rowptr, const float* m, cons
   if (n <= 0) return RBO_OK;
   node_update_tc_kernel<<<tc_grid(n), TNT, TSMEM, st>>>(n, rowptr, m, hin, w, l, agg, rh, hout,
                                                         status);
+  return note_cuda(cudaGetLastError());
+}
+
+
+// Backward of layer l (message or node update); *nblocks = CTAs = partials written
+int layer_back_tc_launch(bool msg, int64_t cnt, int64_t n, const int32_t* erow, const int32_t* col,
+                         const float* g, const float* dagg, const float* act, const float* u0,
+                         const float* u1, const __nv_bfloat16* w, int off_w, float* out0, float* out1,
+                         float* part, int max_blocks, DevStatus* status, cudaStream_t st,
+                         int* nblocks) {
+  *nblocks = 0;
+  if (cnt <= 0) return RBO_OK;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (cnt + TT - 1) / TT;
+  const int G = (int)std::min<int64_t>(std::min<int64_t>(tiles, 2 * (int64_t)std::max(sms, 1)),
+                                        (int64_t)max_blocks);
+  BackArgs P{cnt, n, erow, col, g, dagg, act, u0, u1, w, off_w, out0, out1, part, status};
+  cudaError_t e;
+  if (msg) {
+    e = cudaFuncSetAttribute(layer_back_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, BSMEM);
+    if (e == cudaSuccess) layer_back_tc_kernel<true><<<G, TNT, BSMEM, st>>>(P);
+  } else {
+    e = cudaFuncSetAttribute(layer_back_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, BSMEM);
+    if (e == cudaSuccess) layer_back_tc_kernel<false><<<G, TNT, BSMEM, st>>>(P);
+  }
+  if (e != cudaSuccess) return note_cuda(e);
+  *nblocks = G;
   return note_cuda(cudaGetLastError());
 }
 
