@@ -81,6 +81,52 @@ def test_loss_and_gradient_match_oracle(rbo, problem):
         o += k
 
 
+def _irregular_csr(n=700, seed=21):
+    """Structurally symmetric pattern with very uneven degrees: random pairs, node 0
+    linked to every node (an arrow) and a hub node linked to a third of the nodes, with
+    a dominant diagonal.  Rows of several hundred edges span many of the node layer's
+    16-edge chunks; n is not a multiple of the 128-item tiles."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    hub = n // 2
+    hc = rng.choice(n, n // 3, replace=False)
+    rows = np.concatenate([rng.integers(0, n, 3 * n), np.zeros(n, dtype=np.int64),
+                           np.full(n // 3, hub)])
+    cols = np.concatenate([rng.integers(0, n, 3 * n), np.arange(n), hc])
+    A = sp.coo_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(n, n)).tocsr()
+    A = A + A.T
+    A = A + sp.identity(n) * (4.0 + np.abs(A).sum(axis=1).max())
+    return synth.CSR.from_scipy(sp.csr_matrix(A))
+
+
+def test_forward_and_gradient_irregular_degrees(rbo):
+    import torch
+    A = _irregular_csr()
+    G = ognn.Graph(A)
+    deg = np.diff(A.rowptr)
+    assert deg.max() >= 600 and A.n % 128 != 0 and A.nnz % 128 != 0
+    th = _theta(17)
+    net = rbo.GNN(seed=0)
+    net.set_params(th)
+    Ad = rbo.DeviceCSR.from_host(A)
+    M = net.infer(Ad).cpu().numpy()
+    ref = ognn.forward(th.astype(np.float64), G, bf16=True)
+    assert np.abs(M - ref).max() <= 1e-4 * np.abs(ref).max()
+    R = np.random.default_rng(6).standard_normal((A.n, 4))
+    Rd = rbo.colmajor(A.n, 4)
+    Rd.copy_(torch.from_numpy(R))
+    L, g = net.loss_grad(Ad, Rd)
+    Lr, gr = ognn.loss_and_grad(th.astype(np.float64), G, R, bf16=True)
+    assert abs(L - Lr) <= 1e-5 * abs(Lr)
+    o = 0
+    for name, shp in ognn.param_shapes():
+        k = int(np.prod(shp))
+        ng = np.linalg.norm(gr[o:o + k])
+        if ng > 1e-8 * np.linalg.norm(gr):
+            assert np.linalg.norm(g[o:o + k] - gr[o:o + k]) <= 5e-3 * ng, name
+        o += k
+
+
 def test_adam_training_reduces_loss(rbo, problem):
     import torch
     A, G = problem
