@@ -638,7 +638,7 @@ def run_learned(rbo, torch, args):
             e1.record()
             torch.cuda.synchronize()
             infer_ms = e0.elapsed_time(e1)
-            nnz_eval = A.nnz
+            nnz_eval, n_eval_nodes = A.nnz, A.n
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         x, info, used = learned.solve(net, A, b, jacobi=jac, s=5, s_hat=30, m=60, tol=1e-10)
@@ -655,8 +655,7 @@ def run_learned(rbo, torch, args):
         del A, b, x
     il = float(np.mean([r["iters_learned"] for r in rows]))
     ij_ = float(np.mean([r["iters_jacobi"] for r in rows]))
-    # forward traffic per edge: per layer e (r/w), m (w), h_j gather (r), plus encoders/decoder
-    bytes_infer = nnz_eval * (3 * 4 * 128 + 3 * 128 + 12 + 8)
+    bytes_infer = gnn_infer_bytes(n_eval_nodes, nnz_eval)
     return {"train": {"instances": n_train, "grid": N_train, "epochs": 8,
                       "epoch_loss": hist["epoch_loss"], "train_s": hist["seconds"],
                       "generate_s": t_gen, "loss_grad_ms": grad_ms},
@@ -667,6 +666,18 @@ def run_learned(rbo, torch, args):
                      "rows": rows},
             "infer_ms": infer_ms, "infer_edges": nnz_eval,
             "infer_gbs_algorithmic": bytes_infer / (infer_ms / 1e3) / 1e9 if infer_ms else None}
+
+
+def gnn_infer_bytes(n: int, nnz: int) -> int:
+    """Algorithmic bytes of one inference of the learned-SPAI network (float32
+    activations of width 32 = 128 bytes per row).  Per edge: graph build 56 (column,
+    value, transpose position, features written), 3 message layers 3 x (4 column + 128
+    h_j gathered + 128 m written) + the edge states e_1 written, read, e_2 written, read
+    (512) + 12 features + 4 decoder term written, 3 node updates reading m (3 x 128),
+    decoder 28 (row, column, term, two node terms, M written) -> 1776.  Per node: graph
+    and features 16, encoder 8 + 128, 3 node updates reading h (384) and writing h_1,
+    h_2 (256), decoder terms 8 written, diagonal inverse 8 read, row pointers 16 -> 824."""
+    return 1776 * nnz + 824 * n
 
 
 def run_gnn_kernels(rbo, torch):
@@ -702,6 +713,7 @@ def run_gnn_kernels(rbo, torch):
     R.copy_(torch.from_numpy(np.random.default_rng(2).standard_normal((Bh.n, 8))))
     grad_ms = timed(lambda: net.loss_grad(B, R))
     return {"infer_ms": infer_ms, "infer_n": int(A.n), "infer_edges": int(A.nnz),
+            "infer_gbs_algorithmic": gnn_infer_bytes(A.n, A.nnz) / (infer_ms / 1e3) / 1e9,
             "loss_grad_ms": grad_ms, "loss_grad_n": int(B.n), "loss_grad_edges": int(B.nnz),
             "residual_columns": 8}
 

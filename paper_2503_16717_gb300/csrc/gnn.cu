@@ -103,26 +103,19 @@ __global__ void encode_kernel(int64_t cnt, int nin, const float* __restrict__ in
   out[t] = relu(z);
 }
 
-// decoder: M_e = (wo . [e; h_i; h_j] + bo + [i == j]) / A_ii, warp per edge
-__global__ void decode_kernel(int64_t nnz, const int32_t* __restrict__ erow,
-                              const int32_t* __restrict__ col, const float* __restrict__ e,
-                              const float* __restrict__ h, const __nv_bfloat16* __restrict__ w,
-                              const double* __restrict__ dinv, double* __restrict__ Mval) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const float w0 = bf(w, OFF_WO + lane), w1 = bf(w, OFF_WO + W + lane), w2 = bf(w, OFF_WO + 2 * W + lane);
-  const float bo = bf(w, OFF_BO);
-  for (int64_t q = warp0; q < nnz; q += nwarps) {
-    const int i = erow[q], j = col[q];
-    float s = w0 * e[q * W + lane] + w1 * h[(int64_t)i * W + lane] + w2 * h[(int64_t)j * W + lane];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      const float out = s + bo + (i == j ? 1.f : 0.f);
-      Mval[q] = (double)out * dinv[i];
-    }
-  }
+// decoder: M_e = (wo . [e; h_i; h_j] + bo + [i == j]) / A_ii from the terms the last
+// layers left: pe_e = wo[0:32] . e (message layer), s_i = wo[32:64] . h_i and
+// t_j = wo[64:96] . h_j (node update); thread per edge
+__global__ void decode_terms_kernel(int64_t nnz, const int32_t* __restrict__ erow,
+                                    const int32_t* __restrict__ col, const float* __restrict__ pe,
+                                    const float* __restrict__ sdec, const float* __restrict__ tdec,
+                                    const __nv_bfloat16* __restrict__ w, const double* __restrict__ dinv,
+                                    double* __restrict__ Mval) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nnz) return;
+  const int i = erow[q], j = col[q];
+  const float out = pe[q] + sdec[i] + tdec[j] + bf(w, OFF_BO) + (i == j ? 1.f : 0.f);
+  Mval[q] = (double)out * dinv[i];
 }
 
 // ---- loss (float64) ---------------------------------------------------------------------

@@ -22,14 +22,14 @@ __global__ void graph_features_kernel(int64_t, const int32_t*, const int32_t*, c
                                       const int32_t*, const double*, float*, float*);
 __global__ void encode_kernel(int64_t, int, const float*, const __nv_bfloat16*, int, int, float*);
 // tensor-core message and node-update layers (gnn_tc.cu)
-int message_tc_launch(int64_t nnz, int64_t n, const int32_t* col, const float* ein, const float* h,
-                      const __nv_bfloat16* w, int l, float* m, float* eout, DevStatus* status,
-                      cudaStream_t st);
+int message_tc_launch(int64_t nnz, int64_t n, const int32_t* col, const float* ein, const float* x,
+                      float* e0out, const float* h, const __nv_bfloat16* w, int l, float* m,
+                      float* eout, float* pe, DevStatus* status, cudaStream_t st);
 int node_update_tc_launch(int64_t n, const int32_t* rowptr, const float* m, const float* hin,
                           const __nv_bfloat16* w, int l, float* agg, float* rh, float* hout,
-                          DevStatus* status, cudaStream_t st);
-__global__ void decode_kernel(int64_t, const int32_t*, const int32_t*, const float*, const float*,
-                              const __nv_bfloat16*, const double*, double*);
+                          float* sdec, float* tdec, DevStatus* status, cudaStream_t st);
+__global__ void decode_terms_kernel(int64_t, const int32_t*, const int32_t*, const float*, const float*,
+                                    const float*, const __nv_bfloat16*, const double*, double*);
 __global__ void spmm_kernel(int64_t, int, const int32_t*, const int32_t*, const double*,
                             const double*, int64_t, double*, int64_t);
 __global__ void spmm_t_kernel(int64_t, int, const int32_t*, const int32_t*, const int32_t*,
@@ -175,6 +175,7 @@ struct Work {
   float *x = nullptr, *f = nullptr;
   float *e[NL + 1] = {}, *h[NL + 1] = {}, *m[NL] = {}, *agg[NL] = {}, *rh[NL] = {};
   double* Mval = nullptr;
+  float *pe = nullptr, *sdec = nullptr, *tdec = nullptr;  // decoder terms of the last layer
   // loss / backward
   double *Z = nullptr, *Y = nullptr, *dZ = nullptr, *npart = nullptr, *cscale = nullptr;
   float *dout = nullptr, *de = nullptr, *de2 = nullptr, *dhj = nullptr, *dh = nullptr, *dh2 = nullptr,
@@ -188,6 +189,7 @@ static size_t work_bytes(int64_t n, int64_t nnz, int nr, bool train) {
   b += (size_t)ne * nnz * W * 4 + (size_t)ne * n * W * 4;
   b += (size_t)nm * nnz * W * 4 + (size_t)2 * nm * n * W * 4;
   b += (size_t)nnz * 8;
+  b += (size_t)nnz * 4 + (size_t)2 * n * 4;
   if (train) {
     b += 3 * (size_t)n * nr * 8 + 2 * (size_t)nr * 1024 * 8 + 64 * 8;
     b += (size_t)nnz * 4 + 3 * (size_t)nnz * W * 4 + 3 * (size_t)n * W * 4;
@@ -217,6 +219,9 @@ static int work_take(Arena* ar, Work& w, int64_t n, int64_t nnz, int nr, bool tr
     w.rh[l] = (float*)T(n * W * 4);
   }
   w.Mval = (double*)T(nnz * 8);
+  w.pe = (float*)T(nnz * 4);
+  w.sdec = (float*)T(n * 4);
+  w.tdec = (float*)T(n * 4);
   if (train) {
     w.Z = (double*)T((size_t)n * nr * 8);
     w.Y = (double*)T((size_t)n * nr * 8);
@@ -235,7 +240,8 @@ static int work_take(Arena* ar, Work& w, int64_t n, int64_t nnz, int nr, bool tr
         !w.dh || !w.dh2 || !w.dagg || !w.part)
       return RBO_ERR_NOMEM;
   }
-  if (!w.erow || !w.tpos || !w.dinv || !w.x || !w.f || !w.Mval) return RBO_ERR_NOMEM;
+  if (!w.erow || !w.tpos || !w.dinv || !w.x || !w.f || !w.Mval || !w.pe || !w.sdec || !w.tdec)
+    return RBO_ERR_NOMEM;
   for (int l = 0; l < ne; ++l)
     if (!w.e[l] || !w.h[l]) return RBO_ERR_NOMEM;
   for (int l = 0; l < nm; ++l)
@@ -252,7 +258,9 @@ static unsigned gridw(int64_t items) {  // warp-per-item kernels with 256 thread
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-// graph + forward; with train == false only two activation buffers are kept
+// graph + forward; with train == false only two activation buffers are kept, and only
+// what the next layer reads is written.  The edge encoder runs inside the first message
+// layer; the decoder's dot products inside the last message and node layers.
 static int forward(rbo_gnn_s* g, const rbo_csr* A, Work& w, Arena* ar, cudaStream_t st, bool train,
                    int* launches) {
   const int64_t n = A->n, nnz = A->nnz;
@@ -261,22 +269,26 @@ static int forward(rbo_gnn_s* g, const rbo_csr* A, Work& w, Arena* ar, cudaStrea
   graph_features_kernel<<<grid1(n), 256, 0, st>>>(n, A->rowptr, A->col, A->val, w.tpos, w.dinv, w.x,
                                                   w.f);
   encode_kernel<<<grid1(n * W), 256, 0, st>>>(n, 2, w.f, g->wbf, OFF_WN, OFF_BN, w.h[0]);
-  encode_kernel<<<grid1(nnz * W), 256, 0, st>>>(nnz, 3, w.x, g->wbf, OFF_WE, OFF_BE, w.e[0]);
-  *launches += 4;
+  *launches += 3;
   for (int l = 0; l < NL; ++l) {
     const int a = train ? l : (l & 1), b = train ? l + 1 : ((l + 1) & 1);
+    const bool last = l == NL - 1;
     float* mm = train ? w.m[l] : w.m[0];
-    float* ag = train ? w.agg[l] : w.agg[0];
-    float* rr = train ? w.rh[l] : w.rh[0];
-    int rc = message_tc_launch(nnz, n, A->col, w.e[a], w.h[a], g->wbf, l, mm, w.e[b], ar->status, st);
+    float* ag = train ? w.agg[l] : nullptr;
+    float* rr = train ? w.rh[l] : nullptr;
+    float* eo = (train || !last) ? w.e[b] : nullptr;
+    float* ho = (train || !last) ? w.h[b] : nullptr;
+    int rc = message_tc_launch(nnz, n, A->col, l == 0 ? nullptr : w.e[a], w.x,
+                               (l == 0 && train) ? w.e[0] : nullptr, w.h[a], g->wbf, l, mm, eo,
+                               last ? w.pe : nullptr, ar->status, st);
     if (rc == RBO_OK)
-      rc = node_update_tc_launch(n, A->rowptr, mm, w.h[a], g->wbf, l, ag, rr, w.h[b], ar->status, st);
+      rc = node_update_tc_launch(n, A->rowptr, mm, w.h[a], g->wbf, l, ag, rr, ho,
+                                 last ? w.sdec : nullptr, last ? w.tdec : nullptr, ar->status, st);
     if (rc != RBO_OK) return rc;
     *launches += 2;
   }
-  const int last = train ? NL : (NL & 1);
-  decode_kernel<<<gridw(nnz), 256, 0, st>>>(nnz, w.erow, A->col, w.e[last], w.h[last], g->wbf,
-                                            w.dinv, w.Mval);
+  decode_terms_kernel<<<grid1(nnz), 256, 0, st>>>(nnz, w.erow, A->col, w.pe, w.sdec, w.tdec, g->wbf,
+                                                  w.dinv, w.Mval);
   *launches += 1;
   return note_cuda(cudaGetLastError());
 }

@@ -227,28 +227,53 @@ __device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
 
 }  // namespace
 
-// message layer l over all edges (see the file header); edge q = (row i, col[q] = j)
-__global__ void __launch_bounds__(TNT, TCTAS)
-    message_tc_kernel(int64_t nnz, int64_t n, const int32_t* __restrict__ col,
-                      const float* __restrict__ ein, const float* __restrict__ h,
-                      const __nv_bfloat16* __restrict__ w, int l, float* __restrict__ m,
-                      float* __restrict__ eout, DevStatus* status) {
+// Arguments of a message layer.  The first layer takes the edge features x (3 per edge)
+// instead of e_0 and computes e_0 = relu(We x + be) on the fly (the edge encoder); the
+// last one can leave e_{l+1} unwritten and write the decoder's edge term instead.
+struct MsgArgs {
+  int64_t nnz, n;
+  const int32_t* col;        // column j of edge q
+  const float* ein;          // e_l per edge; null: e_0 from x
+  const float* x;            // edge features, 3 per edge (used when ein is null)
+  float* e0out;              // e_0 written here when computed and non-null
+  const float* h;            // h_l per node (gathered by column)
+  const __nv_bfloat16* w;    // bfloat16 parameters
+  int l;                     // layer
+  float* m;                  // m_l per edge
+  float* eout;               // e_{l+1} = e_l + m_l per edge, or null
+  float* pe;                 // decoder edge term wo[0:32] . e_{l+1} per edge, or null
+  DevStatus* status;
+};
+
+// message layer l over all edges (see the file header); edge q = (row i, col[q] = j).
+// ENC: e_0 from the edge features (first layer); PE: the decoder's edge term (last layer)
+template <bool ENC, bool PE>
+__global__ void __launch_bounds__(TNT, TCTAS) message_tc_kernel(const __grid_constant__ MsgArgs P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_mma, s_fin;
   __shared__ int s_skip;
+  __shared__ float s_bias[32], s_wo[32], s_we[96], s_be[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_skip = read_code(status) != 0;
+  if (tid == 0) s_skip = read_code(P.status) != 0;
   __syncthreads();
   if (s_skip) return;
   unsigned char* smem = align1k(smem_raw);
   float* buf = reinterpret_cast<float*>(smem) + warp * 32 * TLD;
   const unsigned char* Bs = smem + OFF_B;
   if (tid == 0) mbar_init(&s_fin, 1);
-  tc_setup(smem + OFF_B, w, off_wm(l), &s_mma, &s_tmem);
+  tc_setup(smem + OFF_B, P.w, off_wm(P.l), &s_mma, &s_tmem);
   const uint32_t tbase = s_tmem;
   const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
-  const float bias = __bfloat162float(w[off_bm(l) + lane]);
+  const float bias = __bfloat162float(P.w[off_bm(P.l) + lane]);
+  if (warp == 0) {  // layer bias, decoder edge weights, edge encoder (first layer)
+    s_bias[lane] = bias;
+    s_wo[lane] = __bfloat162float(P.w[OFF_WO + lane]);
+    s_be[lane] = __bfloat162float(P.w[OFF_BE + lane]);
+    for (int k = 0; k < 3; ++k) s_we[32 * k + lane] = __bfloat162float(P.w[OFF_WE + 32 * k + lane]);
+  }
+  __syncthreads();
+  const int64_t nnz = P.nnz;
   const int64_t ntiles = (nnz + TT - 1) / TT;
   bool bad = false;
   int it = 0;
@@ -256,8 +281,8 @@ __global__ void __launch_bounds__(TNT, TCTAS)
     const int64_t e0 = tile * TT + warp * 32;
     int cj = -1;
     if (e0 + lane < nnz) {
-      cj = col[e0 + lane];
-      if (cj < 0 || (int64_t)cj >= n) {
+      cj = P.col[e0 + lane];
+      if (cj < 0 || (int64_t)cj >= P.n) {
         bad = true;
         cj = -1;
       }
@@ -266,39 +291,75 @@ __global__ void __launch_bounds__(TNT, TCTAS)
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int c = __shfl_sync(0xffffffffu, cj, j);
-      ev[j] = e0 + j < nnz ? ein[(e0 + j) * W + lane] : 0.f;
-      hv[j] = c >= 0 ? h[(int64_t)c * W + lane] : 0.f;
+      if constexpr (!ENC) ev[j] = e0 + j < nnz ? P.ein[(e0 + j) * W + lane] : 0.f;
+      hv[j] = c >= 0 ? P.h[(int64_t)c * W + lane] : 0.f;
+    }
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;  // first layer: this thread's edge features
+    if (ENC && e0 + lane < nnz) {
+      x0 = P.x[3 * (e0 + lane)];
+      x1 = P.x[3 * (e0 + lane) + 1];
+      x2 = P.x[3 * (e0 + lane) + 2];
     }
     __syncwarp();  // the previous tile's reads of the buffer are done
+    if constexpr (ENC) {
+      // the edge encoder for this thread's edge, in the order of its own kernel (bias,
+      // then inputs 0..2), into its buffer row
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      buf[j * TLD + lane] = ev[j];
-      buf[j * TLD + 32 + lane] = hv[j];
+      for (int c = 0; c < 32; ++c) {
+        float z = s_be[c];
+        z = fmaf(s_we[3 * c], x0, z);
+        z = fmaf(s_we[3 * c + 1], x1, z);
+        z = fmaf(s_we[3 * c + 2], x2, z);
+        buf[lane * TLD + c] = e0 + lane < nnz ? relu_tc(z) : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) buf[j * TLD + lane] = ev[j];
     }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) buf[j * TLD + 32 + lane] = hv[j];
     __syncwarp();
+    if (ENC && P.e0out) {
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j)
+        if (e0 + j < nnz) P.e0out[(e0 + j) * W + lane] = buf[j * TLD + lane];
+    }
     if (!tile_products(buf, tbase, tlane, Bs, &s_mma, it)) {
-      if (tid == 0) set_error(status, RBO_ERR_TIMEOUT, 40);
+      if (tid == 0) set_error(P.status, RBO_ERR_TIMEOUT, 40);
       break;
     }
+    if constexpr (PE) {  // this thread's edge: wo[0:32] . e_{l+1} from its buffer row
+      float t = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float mv = relu_tc(buf[lane * TLD + 32 + c] + s_bias[c]);
+        t = fmaf(s_wo[c], buf[lane * TLD + c] + mv, t);
+      }
+      if (e0 + lane < nnz) P.pe[e0 + lane] = t;
+    }
+    float* __restrict__ eout = P.eout;
 #pragma unroll 8
     for (int j = 0; j < 32; ++j) {
       if (e0 + j < nnz) {
         const float mv = relu_tc(buf[j * TLD + 32 + lane] + bias);
-        m[(e0 + j) * W + lane] = mv;
-        eout[(e0 + j) * W + lane] = buf[j * TLD + lane] + mv;
+        P.m[(e0 + j) * W + lane] = mv;
+        if (eout) eout[(e0 + j) * W + lane] = buf[j * TLD + lane] + mv;
       }
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(status, RBO_ERR_ARG, 41);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.status, RBO_ERR_ARG, 41);
   tc_teardown(&s_fin, tbase);
 }
 
 // aggregation + node update of layer l over all nodes (see the file header)
+// agg, rh and hout may be null (inference keeps only what the next layer reads); sdec
+// and tdec, when non-null, receive the decoder's node terms wo[32:64] . h' and
+// wo[64:96] . h' (the last layer)
 __global__ void __launch_bounds__(TNT, TCTAS)
     node_update_tc_kernel(int64_t n, const int32_t* __restrict__ rowptr, const float* __restrict__ m,
                           const float* __restrict__ hin, const __nv_bfloat16* __restrict__ w, int l,
                           float* __restrict__ agg, float* __restrict__ rh, float* __restrict__ hout,
-                          DevStatus* status) {
+                          float* __restrict__ sdec, float* __restrict__ tdec, DevStatus* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_mma, s_fin;
@@ -315,6 +376,13 @@ __global__ void __launch_bounds__(TNT, TCTAS)
   const uint32_t tbase = s_tmem;
   const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
   const float bias = __bfloat162float(w[off_bh(l) + lane]);
+  __shared__ float s_bias[32], s_woi[32], s_woj[32];
+  if (warp == 0) {  // read after the first tile's barriers
+    s_bias[lane] = bias;
+    s_woi[lane] = __bfloat162float(w[OFF_WO + W + lane]);
+    s_woj[lane] = __bfloat162float(w[OFF_WO + 2 * W + lane]);
+  }
+  __syncthreads();
   const int64_t ntiles = (n + TT - 1) / TT;
   int it = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -357,20 +425,35 @@ __global__ void __launch_bounds__(TNT, TCTAS)
 #pragma unroll
     for (int j = 0; j < 32; ++j) buf[j * TLD + lane] = hv[j];
     __syncwarp();
+    if (agg) {
 #pragma unroll 8
-    for (int j = 0; j < 32; ++j)
-      if (i0 + j < n) agg[(i0 + j) * W + lane] = buf[j * TLD + 32 + lane];
+      for (int j = 0; j < 32; ++j)
+        if (i0 + j < n) agg[(i0 + j) * W + lane] = buf[j * TLD + 32 + lane];
+    }
     __syncwarp();  // agg read before tile_products overwrites the columns with outputs
     if (!tile_products(buf, tbase, tlane, Bs, &s_mma, it)) {
       if (tid == 0) set_error(status, RBO_ERR_TIMEOUT, 42);
       break;
     }
+    if (sdec) {  // this thread's node: wo[32:64] . h' and wo[64:96] . h' from its buffer row
+      float si = 0.f, tj = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float hn = buf[lane * TLD + c] + relu_tc(buf[lane * TLD + 32 + c] + s_bias[c]);
+        si = fmaf(s_woi[c], hn, si);
+        tj = fmaf(s_woj[c], hn, tj);
+      }
+      if (i0 + lane < n) {
+        sdec[i0 + lane] = si;
+        tdec[i0 + lane] = tj;
+      }
+    }
 #pragma unroll 8
     for (int j = 0; j < 32; ++j) {
       if (i0 + j < n) {
         const float r = relu_tc(buf[j * TLD + 32 + lane] + bias);
-        rh[(i0 + j) * W + lane] = r;
-        hout[(i0 + j) * W + lane] = buf[j * TLD + lane] + r;
+        if (rh) rh[(i0 + j) * W + lane] = r;
+        if (hout) hout[(i0 + j) * W + lane] = buf[j * TLD + lane] + r;
       }
     }
   }
@@ -657,23 +740,31 @@ static int tc_grid(int64_t items) {
   return (int)std::min<int64_t>(tiles, (int64_t)TCTAS * std::max(sms, 1));
 }
 
-int message_tc_launch(int64_t nnz, int64_t n, const int32_t* col, const float* ein, const float* h,
-                      const __nv_bfloat16* w, int l, float* m, float* eout, DevStatus* status,
-                      cudaStream_t st) {
+int message_tc_launch(int64_t nnz, int64_t n, const int32_t* col, const float* ein, const float* x,
+                      float* e0out, const float* h, const __nv_bfloat16* w, int l, float* m,
+                      float* eout, float* pe, DevStatus* status, cudaStream_t st) {
   if (nnz <= 0) return RBO_OK;
-  message_tc_kernel<<<tc_grid(nnz), TNT, TSMEM, st>>>(nnz, n, col, ein, h, w, l, m, eout, status);
+  const MsgArgs P{nnz, n, col, ein, x, e0out, h, w, l, m, eout, pe, status};
+  const int G = tc_grid(nnz);
+  if (!ein && pe)
+    message_tc_kernel<true, true><<<G, TNT, TSMEM, st>>>(P);
+  else if (!ein)
+    message_tc_kernel<true, false><<<G, TNT, TSMEM, st>>>(P);
+  else if (pe)
+    message_tc_kernel<false, true><<<G, TNT, TSMEM, st>>>(P);
+  else
+    message_tc_kernel<false, false><<<G, TNT, TSMEM, st>>>(P);
   return note_cuda(cudaGetLastError());
 }
 
 int node_update_tc_launch(int64_t n, const int32_t* rowptr, const float* m, const float* hin,
                           const __nv_bfloat16* w, int l, float* agg, float* rh, float* hout,
-                          DevStatus* status, cudaStream_t st) {
+                          float* sdec, float* tdec, DevStatus* status, cudaStream_t st) {
   if (n <= 0) return RBO_OK;
-  node_update_tc_kernel<<<tc_grid(n), TNT, TSMEM, st>>>(n, rowptr, m, hin, w, l, agg, rh, hout,
-                                                        status);
+  node_update_tc_kernel<<<tc_grid(n), TNT, TSMEM, st>>>(n, rowptr, m, hin, w, l, agg, rh, hout, sdec,
+                                                        tdec, status);
   return note_cuda(cudaGetLastError());
 }
-
 
 // Backward of layer l (message or node update); *nblocks = CTAs = partials written
 int layer_back_tc_launch(bool msg, int64_t cnt, int64_t n, const int32_t* erow, const int32_t* col,
