@@ -17,7 +17,8 @@
 // Work of one CTA (128 threads, 4 warps; warp q owns tensor-memory lanes 32q..32q+31 =
 // items 32q..32q+31 of the tile), per tile:
 //   1. the warp loads its 32 items' inputs with lane = channel (coalesced 128-byte rows;
-//      the node layer also sums each node's incoming messages, edges in CSR order) into
+//      the node layer also sums each node's incoming messages, edges in CSR order, 32
+//      message rows in flight per warp) into
 //      a per-warp buffer with row = item (stride 65 floats: the lane = channel writes and
 //      the row-per-thread reads are both free of bank conflicts);
 //   2. thread t reads row t, splits it and stores the pieces to tensor memory (A: piece p
@@ -392,23 +393,28 @@ __global__ void __launch_bounds__(TNT, TCTAS)
     const int rs = rowptr[std::min<int64_t>(i0 + lane, n)];
     const int E0 = __shfl_sync(0xffffffffu, rs, 0);
     const int E1 = rowptr[std::min<int64_t>(i0 + 32, n)];
-    float hv[32];
+    {
+      float hv[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) hv[j] = i0 + j < n ? hin[(i0 + j) * W + lane] : 0.f;
-    __syncwarp();  // the previous tile's reads of the buffer are done
+      for (int j = 0; j < 32; ++j) hv[j] = i0 + j < n ? hin[(i0 + j) * W + lane] : 0.f;
+      __syncwarp();  // the previous tile's reads of the buffer are done
 #pragma unroll
-    for (int j = 0; j < 32; ++j) buf[j * TLD + 32 + lane] = 0.f;  // nodes without edges
-    // incoming messages in CSR order, 16 edges in flight; an edge belongs to the last node
+      for (int j = 0; j < 32; ++j) {
+        buf[j * TLD + lane] = hv[j];
+        buf[j * TLD + 32 + lane] = 0.f;  // nodes without edges
+      }
+    }
+    // incoming messages in CSR order, 32 edges in flight; an edge belongs to the last node
     // whose row starts at or before it; each node's sum starts from 0 and adds its edges
     // in order
     int cur = -1;
     float run = 0.f;
-    for (int e = E0; e < E1; e += 16) {
-      float v[16];
+    for (int e = E0; e < E1; e += 32) {
+      float v[32];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = e + u < E1 ? m[(int64_t)(e + u) * W + lane] : 0.f;
+      for (int u = 0; u < 32; ++u) v[u] = e + u < E1 ? m[(int64_t)(e + u) * W + lane] : 0.f;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
+      for (int u = 0; u < 32; ++u) {
         if (e + u < E1) {
           const unsigned mask = __ballot_sync(0xffffffffu, rs <= e + u);
           const int j = 31 - __clz((int)mask);
@@ -422,8 +428,6 @@ __global__ void __launch_bounds__(TNT, TCTAS)
       }
     }
     if (cur >= 0) buf[cur * TLD + 32 + lane] = run;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) buf[j * TLD + lane] = hv[j];
     __syncwarp();
     if (agg) {
 #pragma unroll 8
