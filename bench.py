@@ -680,9 +680,10 @@ def gnn_infer_bytes(n: int, nnz: int) -> int:
     return 1776 * nnz + 824 * n
 
 
-def run_gnn_kernels(rbo, torch):
+def run_gnn_kernels(rbo, torch, grid: int = 2048):
     """Kernel times of the learned-SPAI network alone (--gnn-only): one inference on an
-    unseen 2048^2 convection-diffusion instance (n = 4.19M, 21M edges) and one loss and
+    unseen grid^2 convection-diffusion instance (2048^2 by default: n = 4.19M, 21M
+    edges; --gnn-grid sets the grid) and one loss and
     gradient on a 512^2 training instance with 8 residual columns, each timed with CUDA
     events over 5 calls after a warm-up call.  Weights: the initial ones plus seeded
     N(0, 0.05^2) noise (the cost does not depend on their values)."""
@@ -704,7 +705,7 @@ def run_gnn_kernels(rbo, torch):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    Ah, _ = synth.convdiff2d_csr(2048, 4000)
+    Ah, _ = synth.convdiff2d_csr(grid, 4000)
     A = rbo.DeviceCSR.from_host(Ah)
     infer_ms = timed(lambda: net.infer(A))
     Bh, _ = synth.convdiff2d_csr(512, 3000)
@@ -980,11 +981,13 @@ def main():
     ap.add_argument("--gnn-only", action="store_true",
                     help="only time the learned-SPAI network's inference (2048^2) and loss and "
                          "gradient (512^2), print them as one JSON object and exit")
+    ap.add_argument("--gnn-grid", type=int, default=2048,
+                    help="grid points per side of the --gnn-only inference instance")
     args = ap.parse_args()
     if args.gnn_only:
         import torch
         import paper_2503_16717_gb300 as rbo
-        print(json.dumps({"gnn_kernels": run_gnn_kernels(rbo, torch)}), flush=True)
+        print(json.dumps({"gnn_kernels": run_gnn_kernels(rbo, torch, args.gnn_grid)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
