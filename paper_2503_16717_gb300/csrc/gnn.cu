@@ -230,14 +230,30 @@ __global__ void decode_back_edges_kernel(int64_t nnz, const int32_t* __restrict_
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float w0 = bf(w, OFF_WO + lane);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};  // g_wo[lane], g_wo[32+lane], g_wo[64+lane], g_bo (lane 0)
-  for (int64_t q = warp0; q < nnz; q += nwarps) {
-    const int i = erow[q], j = col[q];
-    const float d = dout[q];
-    acc[0] = fmaf(d, e[q * W + lane], acc[0]);
-    acc[1] = fmaf(d, h[(int64_t)i * W + lane], acc[1]);
-    acc[2] = fmaf(d, h[(int64_t)j * W + lane], acc[2]);
-    if (lane == 0) acc[3] += d;
-    de[q * W + lane] = d * w0;
+  // edges warp0, warp0 + nwarps, ... in order, the loads of 4 of them issued together
+  for (int64_t q0 = warp0; q0 < nnz; q0 += 4 * nwarps) {
+    float d[4], ev[4], hi[4], hj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t q = q0 + u * nwarps;
+      const bool v = q < nnz;
+      const int i = v ? erow[q] : 0, j = v ? col[q] : 0;
+      d[u] = v ? dout[q] : 0.f;
+      ev[u] = v ? e[q * W + lane] : 0.f;
+      hi[u] = v ? h[(int64_t)i * W + lane] : 0.f;
+      hj[u] = v ? h[(int64_t)j * W + lane] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t q = q0 + u * nwarps;
+      if (q < nnz) {
+        acc[0] = fmaf(d[u], ev[u], acc[0]);
+        acc[1] = fmaf(d[u], hi[u], acc[1]);
+        acc[2] = fmaf(d[u], hj[u], acc[2]);
+        if (lane == 0) acc[3] += d[u];
+        de[q * W + lane] = d[u] * w0;
+      }
+    }
   }
   block_partial_store(acc, 128, sred, part);
 }
@@ -272,38 +288,68 @@ __global__ void gather_cols_kernel(int64_t n, const int32_t* __restrict__ rowptr
   dhl[t] = s;
 }
 
-// encoder backward: dz = d * [out > 0]; g_W[c][k] += dz x_k, g_b[c] += dz; one thread
-// per channel c and input k (plus bias), looping over all items in fixed order within
-// a block, blocks striding over items.
-__global__ void encode_back_kernel(int64_t cnt, int nin, const float* __restrict__ in,
-                                   const float* __restrict__ out, const float* __restrict__ d,
-                                   float* __restrict__ part) {
-  // thread layout: lane = channel c, warp w handles items w, w + nw, ...
-  extern __shared__ float sred[];
+// encoder backward: dz = d * [out > 0]; g_W[c][k] += dz x_k, g_b[c] += dz (NIN inputs per
+// item); lane = channel c, warp w handles items w, w + nw, ... in order, the loads of 4
+// items issued together; blocks stride over items
+template <int NIN>
+__device__ __forceinline__ void encode_back_body(int64_t cnt, const float* __restrict__ in,
+                                                 const float* __restrict__ out,
+                                                 const float* __restrict__ d, float* __restrict__ part,
+                                                 float* sred) {
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   float acc[32];
 #pragma unroll
   for (int k = 0; k < 32; ++k) acc[k] = 0.f;
-  for (int64_t it = warp0; it < cnt; it += nwarps) {
-    const float dz = out[it * W + lane] > 0.f ? d[it * W + lane] : 0.f;
-    for (int k = 0; k < nin; ++k) acc[k] = fmaf(dz, in[it * nin + k], acc[k]);
-    acc[nin] += dz;
+  for (int64_t it0 = warp0; it0 < cnt; it0 += 4 * nwarps) {
+    float dz[4], x[4][NIN];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t it = it0 + u * nwarps;
+      const bool v = it < cnt;
+      const float o = v ? out[it * W + lane] : 0.f;
+      const float g = v ? d[it * W + lane] : 0.f;
+      dz[u] = o > 0.f ? g : 0.f;
+#pragma unroll
+      for (int k = 0; k < NIN; ++k) x[u][k] = v ? in[it * NIN + k] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < NIN; ++k) acc[k] = fmaf(dz[u], x[u][k], acc[k]);
+      acc[NIN] += dz[u];
+    }
   }
   block_partial_store(acc, 32 * 32, sred, part);
 }
+// edge encoder (3 features per edge) and node encoder (2 features per node)
+__global__ void encode_back_edges_kernel(int64_t cnt, const float* __restrict__ in,
+                                         const float* __restrict__ out, const float* __restrict__ d,
+                                         float* __restrict__ part) {
+  extern __shared__ float sred[];
+  encode_back_body<3>(cnt, in, out, d, part, sred);
+}
+__global__ void encode_back_nodes_kernel(int64_t cnt, const float* __restrict__ in,
+                                         const float* __restrict__ out, const float* __restrict__ d,
+                                         float* __restrict__ part) {
+  extern __shared__ float sred[];
+  encode_back_body<2>(cnt, in, out, d, part, sred);
+}
 
-// grad[dst[k]] = sum over blocks of part[b][src[k]] (fixed block order)
+// grad[dst[k]] = sum over blocks of part[b][src[k]]: one warp per output, lane l adds
+// blocks l, l + 32, ... in order, then a fixed butterfly over the lanes (deterministic)
 __global__ void reduce_partials_kernel(const float* __restrict__ part, int nblocks, int cnt,
                                        const int* __restrict__ map_src, const int* __restrict__ map_dst,
                                        int nmap, float* __restrict__ grad) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= nmap) return;
   const int s = map_src[t];
   float acc = 0.f;
-  for (int b = 0; b < nblocks; ++b) acc += part[(int64_t)b * cnt + s];
-  grad[map_dst[t]] = acc;
+  for (int b = lane; b < nblocks; b += 32) acc += part[(int64_t)b * cnt + s];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) grad[map_dst[t]] = acc;
 }
 
 __global__ void adam_kernel(int np, float* __restrict__ th, const float* __restrict__ g,

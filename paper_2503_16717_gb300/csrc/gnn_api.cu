@@ -50,7 +50,8 @@ int layer_back_tc_launch(bool msg, int64_t cnt, int64_t n, const int32_t* erow, 
                          float* part, int max_blocks, DevStatus* status, cudaStream_t st,
                          int* nblocks);
 __global__ void gather_cols_kernel(int64_t, const int32_t*, const int32_t*, const float*, float*);
-__global__ void encode_back_kernel(int64_t, int, const float*, const float*, const float*, float*);
+__global__ void encode_back_edges_kernel(int64_t, const float*, const float*, const float*, float*);
+__global__ void encode_back_nodes_kernel(int64_t, const float*, const float*, const float*, float*);
 __global__ void reduce_partials_kernel(const float*, int, int, const int*, const int*, int, float*);
 __global__ void adam_kernel(int, float*, const float*, float*, float*, float, float, float, float,
                             float, float, __nv_bfloat16*);
@@ -295,7 +296,7 @@ static int forward(rbo_gnn_s* g, const rbo_csr* A, Work& w, Arena* ar, cudaStrea
 
 static void reduce_group(const Map& m, const float* part, float* grad, cudaStream_t st,
                          int nblocks = NBLK_RED) {
-  reduce_partials_kernel<<<grid1(m.nmap), 256, 0, st>>>(part, nblocks, m.cnt, m.src, m.dst, m.nmap,
+  reduce_partials_kernel<<<grid1((int64_t)m.nmap * 32), 256, 0, st>>>(part, nblocks, m.cnt, m.src, m.dst, m.nmap,
                                                         grad);
 }
 
@@ -367,9 +368,9 @@ static int loss_grad(rbo_gnn_s* g, const rbo_csr* A, const double* R, int nr, in
     std::swap(dh, dhn);
     std::swap(de, den);
   }
-  encode_back_kernel<<<NBLK_RED, BLK, sm_enc, st>>>(nnz, 3, w.x, w.e[0], de, w.part);
+  encode_back_edges_kernel<<<NBLK_RED, BLK, sm_enc, st>>>(nnz, w.x, w.e[0], de, w.part);
   reduce_group(g->enc_e, w.part, g->grad, st);
-  encode_back_kernel<<<NBLK_RED, BLK, sm_enc, st>>>(n, 2, w.f, w.h[0], dh, w.part);
+  encode_back_nodes_kernel<<<NBLK_RED, BLK, sm_enc, st>>>(n, w.f, w.h[0], dh, w.part);
   reduce_group(g->enc_n, w.part, g->grad, st);
   *launches += 4;
   *arp = ar;

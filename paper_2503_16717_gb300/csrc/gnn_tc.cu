@@ -415,16 +415,15 @@ __global__ void __launch_bounds__(TNT, TCTAS)
       for (int u = 0; u < 32; ++u) v[u] = e + u < E1 ? m[(int64_t)(e + u) * W + lane] : 0.f;
 #pragma unroll
       for (int u = 0; u < 32; ++u) {
-        if (e + u < E1) {
-          const unsigned mask = __ballot_sync(0xffffffffu, rs <= e + u);
-          const int j = 31 - __clz((int)mask);
-          if (j != cur) {
-            if (cur >= 0) buf[cur * TLD + 32 + lane] = run;
-            run = 0.f;
-            cur = j;
-          }
-          run += v[u];
-        }
+        // branch-free: a new node stores the previous node's sum and restarts from this
+        // edge (0 + v = v, the same value as an explicit restart); edges past the range
+        // keep the node and add 0
+        const unsigned mask = __ballot_sync(0xffffffffu, rs <= e + u);
+        const int j = e + u < E1 ? 31 - __clz((int)mask) : cur;
+        const bool fresh = j != cur;
+        if (fresh && cur >= 0) buf[cur * TLD + 32 + lane] = run;
+        run = fresh ? v[u] : run + v[u];
+        cur = j;
       }
     }
     if (cur >= 0) buf[cur * TLD + 32 + lane] = run;
