@@ -13,6 +13,11 @@ Also reported (the block orthogonalization alone, V = 2^24 x 61 glued blocks,
 two-stage s_hat = 30 and one-stage, FP64 and mixed precision): orthogonalized
 columns/s, algorithmic HBM GB/s and ||I - Q^T Q||_2, under "orth".
 
+At one GPU it also runs the stress workload's two-stage solves (3D convection-diffusion
+256^3, s=10, s_hat=50, m=100, float64 and mixed precision, learned SPAI with Jacobi
+fallback) under "stress"; --stress adds the one-stage and Jacobi-only runs, --no-stress
+skips it.
+
 `--impl reference` times the CPU oracle (numpy/scipy) on a bounded sample of the
 same workload and prints the same JSON line with "impl": "reference".
 """
@@ -256,7 +261,9 @@ def run_ours(args):
 
     orth = run_orth(rbo, torch, args) if (rank == 0 and not args.no_orth) else None
     learned_res = run_learned(rbo, torch, args) if (rank == 0 and not args.no_learned) else None
-    stress_res = run_stress(rbo, torch, args) if (rank == 0 and args.stress) else None
+    stress_res = None
+    if rank == 0 and (args.stress or (world == 1 and not args.no_stress)):
+        stress_res = run_stress(rbo, torch, args, core_only=not args.stress)
     bases_res = run_stress_bases(rbo, torch, args) if (rank == 0 and args.stress_bases) else None
     sweep_res = run_s_sweep(rbo, torch, Ad, bd, args) if (rank == 0 and args.s_sweep) else None
     cpu = None
@@ -747,12 +754,14 @@ def run_s_sweep(rbo, torch, Ad, bd, args):
     return out
 
 
-def run_stress(rbo, torch, args):
+def run_stress(rbo, torch, args, core_only=False):
     """Nonsymmetric 3D convection-diffusion, 7-point upwind, anisotropy (1, 1, 1e-3),
     Peclet 100 (seed 7), N^3 cells; s-step GMRES(m=100, s=10) to 1e-10:
     one-stage with CholQR2 (the deterministic baseline) and with RandCholQR, then two-stage
     RandBCGS2 (s_hat=50) in float64 and mixed precision with Jacobi and with the
-    learned SPAI (trained on smaller instances of the family; Jacobi fallback)."""
+    learned SPAI (trained on smaller instances of the family; Jacobi fallback).
+    core_only (the default run at one GPU): only the two-stage float64 and mixed solves
+    with the learned SPAI and its Jacobi fallback, the runs the stress workload names."""
     import numpy as np
     import synth
     from paper_2503_16717_gb300 import learned
@@ -783,15 +792,17 @@ def run_stress(rbo, torch, args):
         d.update(kw)
         return d
 
-    # the deterministic baseline: one-stage with CholQR2 on the monomial panels
-    (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10,
-                                                   max_restarts=args.stress_restarts,
-                                                   intra=rbo.INTRA_CHOLQR2))
-    out["cholqr2_one_stage"] = row(info, sec)
-    # the randomized one-stage scheme on the same panels
-    (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10,
-                                                   max_restarts=args.stress_restarts))
-    out["randcholqr_one_stage"] = row(info, sec)
+    out["core_only"] = core_only
+    if not core_only:
+        # the deterministic baseline: one-stage with CholQR2 on the monomial panels
+        (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10,
+                                                       max_restarts=args.stress_restarts,
+                                                       intra=rbo.INTRA_CHOLQR2))
+        out["cholqr2_one_stage"] = row(info, sec)
+        # the randomized one-stage scheme on the same panels
+        (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, m=100, tol=1e-10,
+                                                       max_restarts=args.stress_restarts))
+        out["randcholqr_one_stage"] = row(info, sec)
     # the learned SPAI, trained on the same family at 48^3
     t0 = time.perf_counter()
     train_set = learned.make_instances(lambda n_, sd: synth.convdiff3d_csr(n_, sd), range(100, 116), 48,
@@ -804,10 +815,11 @@ def run_stress(rbo, torch, args):
     jac = rbo.GNN(seed=0)
     runs = []
     for prec, pn in ((rbo.PREC_FP64, "fp64"), (rbo.PREC_MIXED, "mixed")):
-        (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, s_hat=50, m=100, tol=1e-10,
-                                                       precision=prec,
-                                                       max_restarts=args.stress_restarts))
-        runs.append(row(info, sec, precision=pn, precond="jacobi"))
+        if not core_only:
+            (_, info), sec = timed(lambda: rbo.sstep_gmres(A, b, s=10, s_hat=50, m=100,
+                                                           tol=1e-10, precision=prec,
+                                                           max_restarts=args.stress_restarts))
+            runs.append(row(info, sec, precision=pn, precond="jacobi"))
         (res, sec) = timed(lambda: learned.solve(net, A, b, jacobi=jac, s=10, s_hat=50, m=100,
                                                  tol=1e-10, precision=prec,
                                                  max_restarts=args.stress_restarts))
@@ -970,7 +982,12 @@ def main():
     ap.add_argument("--learned-full", action="store_true")
     ap.add_argument("--learned-quick", action="store_true")
     ap.add_argument("--stress", action="store_true",
-                    help="also run the 3D convection-diffusion stress solve (s=10, s_hat=50, m=100)")
+                    help="the full 3D convection-diffusion stress study (s=10, s_hat=50, m=100): "
+                         "also the one-stage CholQR2 and RandCholQR runs and the Jacobi-only "
+                         "two-stage runs; without it a run on one GPU does the two-stage float64 "
+                         "and mixed solves with the learned SPAI")
+    ap.add_argument("--no-stress", action="store_true",
+                    help="skip the stress solves of the default run")
     ap.add_argument("--stress-n", type=int, default=256, help="grid points per side of the stress case")
     ap.add_argument("--stress-restarts", type=int, default=100)
     ap.add_argument("--stress-bases", action="store_true",
