@@ -18,9 +18,9 @@
 // items 32q..32q+31 of the tile), per tile:
 //   1. the warp loads its 32 items' inputs with lane = channel (coalesced 128-byte rows;
 //      the node layer also sums each node's incoming messages, edges in CSR order, 32
-//      message rows in flight per warp) into
-//      a per-warp buffer with row = item (stride 65 floats: the lane = channel writes and
-//      the row-per-thread reads are both free of bank conflicts);
+//      message rows in flight per warp) into a per-warp buffer with row = item (stride
+//      65 floats: the lane = channel writes and the row-per-thread reads are both free
+//      of bank conflicts);
 //   2. thread t reads row t, splits it and stores the pieces to tensor memory (A: piece p
 //      at columns 32p..32p+31, two bfloat16 per 32-bit column in K order);
 //   3. one thread issues the 12 MMAs (3 pieces x 4 K-steps of 16) into D (columns
@@ -29,6 +29,10 @@
 //      with lane = channel for the epilogue and coalesced stores.
 // Four CTAs per SM (a quarter of tensor memory each) overlap one CTA's loads with
 // another's products.  Every wait is bounded; a timeout sets RBO_ERR_TIMEOUT.
+// In inference the first message layer computes e_0 from the edge features (the edge
+// encoder) and the last message and node layers compute the decoder's dot products, so
+// neither e_0 nor the last e and h need to be stored.  The backward of both layers (two
+// more contractions per tile) follows the forward kernels below.
 #include <cuda_bf16.h>
 
 #include <algorithm>
