@@ -351,7 +351,10 @@ int rbo_sstep_gmres_precond(const rbo_csr* A, const double* Mval, const double* 
  * pattern (RBO_ERR_ARG otherwise).  The handle owns ~0.3 MB of device memory;
  * calls use the per-device workspace arena.  Parameters are a flat float vector of
  * rbo_gnn_param_count() values in the order Wn(32x2) bn We(32x3) be, then per layer
- * Wm(32x64) bm Wh(32x64) bh, then wo(96) bo (row-major matrices).              */
+ * Wm(32x64) bm Wh(32x64) bh, then wo(96) bo (row-major matrices).  The message and
+ * node layers and their backward run on the tensor cores: each FP32 activation is
+ * split into three BF16 pieces, whose products with the BF16 weights are exact, and
+ * the sums are FP32, so the results agree with an FP32 evaluation.              */
 typedef struct rbo_gnn_s* rbo_gnn;
 int rbo_gnn_param_count(void);
 /* Random He-scaled hidden weights from `seed`, zero biases and output layer.       */
