@@ -9,10 +9,11 @@
 // done here by tcgen05.mma with M = 128 items, N = 32 outputs, K = 64 inputs.
 //
 // Precision.  X is float32.  Every value is split into three bfloat16 pieces,
-// x = x0 + x1 + x2 + r with x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1) (each
-// difference is exact in float32) and |r| <= 2^-27 |x|, below float32's own rounding.  A
-// piece times a bfloat16 weight is exact in float32, so Z = [X0 X1 X2] [W W W]^T (K = 192)
-// is X W^T to float32 accuracy, summed in the tensor core's float32 accumulator.
+// x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1): each difference is exact in
+// float32, and x = x0 + x1 + x2 exactly (x has 24 significant bits, the first remainder
+// at most 16, the second at most 8, which bfloat16 holds).  A piece times a bfloat16
+// weight is exact in float32, so Z = [X0 X1 X2] [W W W]^T (K = 192) is X W^T with only
+// the float32 rounding of the tensor core's accumulator.
 //
 // Work of one CTA (128 threads, 4 warps; warp q owns tensor-memory lanes 32q..32q+31 =
 // items 32q..32q+31 of the tile), per tile:
@@ -479,8 +480,9 @@ __global__ void __launch_bounds__(TNT, TCTAS)
 //   dW^T (M = 128 = (piece p of u, input k), N = 64 = (piece q of dz, output c), K = the
 //     tile's items): A = the hi (p = 0) and lo (p = 1) bfloat16 pieces of u, row (p, k),
 //     two items per 32-bit column; B = the hi and lo pieces of dz (shared memory, K = item);
-//     accumulated in tensor memory over all tiles of the CTA.  The four piece products sum
-//     to u dz^T within about 2^-16 relative per term.
+//     accumulated in tensor memory over all tiles of the CTA.  The hi/lo split leaves a
+//     remainder below 2^-16 of each value, so the four piece products sum to u dz^T
+//     within 2^-15 relative per term.
 // At the end each CTA writes its partial of dW (element (c, k) at k * 32 + c) and db
 // (at 64 * 32 + c), summed over the CTAs in a fixed order by the reduction kernel.
 struct BackArgs {
