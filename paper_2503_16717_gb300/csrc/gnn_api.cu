@@ -254,10 +254,6 @@ static unsigned grid1(int64_t threads, int bs = 256) {
   int64_t b = (threads + bs - 1) / bs;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 30));
 }
-static unsigned gridw(int64_t items) {  // warp-per-item kernels with 256 threads
-  int64_t b = (items + 7) / 8;
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
-}
 
 // graph + forward; with train == false only two activation buffers are kept, and only
 // what the next layer reads is written.  The edge encoder runs inside the first message
