@@ -499,6 +499,33 @@ def _orth_vs_oracle(rbo, torch, V0, c, s, s_hat, nrows=20000):
     return out
 
 
+def _orth_oracle_timing(torch, V0, c, s, s_hat, nrows=1 << 20):
+    """The CPU oracle's block orthogonalization of the workload, timed on its first
+    `nrows` rows (one-stage and two-stage, the same sketch parameters) and scaled
+    linearly to the full row count: every step of both schemes is a pass over the rows
+    or a small factorisation, so the time grows in proportion to n.  A labelled
+    estimate, on the host cores."""
+    from oracle import orth
+    from oracle.sketch import Sketch as OSketch
+    n = V0.shape[1]
+    nrows = min(nrows, n)
+    Vh = V0[:, :nrows].t().contiguous().cpu().numpy()      # nrows x c
+    osk = OSketch(nrows, 4 * c, 8, 42)
+    t = {}
+    for scheme in ("one", "two"):
+        t0 = time.perf_counter()
+        if scheme == "one":
+            orth.block_orth_one_stage(Vh, s, osk, v0=True)
+        else:
+            orth.block_orth_two_stage(Vh, s, s_hat, osk, v0=True)
+        t[scheme] = time.perf_counter() - t0
+    scale = n / nrows
+    return {"kind": "oracle", "estimate": True, "rows_sampled": nrows, "rows": n,
+            "cores": _cpu_threads(),
+            "sample_s": t, "est_s": {k: v * scale for k, v in t.items()},
+            "est_cols_per_s": {k: c / (v * scale) for k, v in t.items()}}
+
+
 def run_orth(rbo, torch, args):
     """Block orthogonalization alone on V = 2^24 x 61 (v0 + 12 glued blocks of 5).
 
@@ -519,6 +546,7 @@ def run_orth(rbo, torch, args):
     W = torch.empty_like(V0)
     Q64 = torch.empty_like(V0)
     vs_oracle = None
+    oracle_time = None
     for kappa in kappas:
         if kappa != kappas[0]:
             del V0
@@ -526,6 +554,7 @@ def run_orth(rbo, torch, args):
             V0 = synth.glued_blocks_torch(n, nb, s, kappa, seed=1, v0=True, device="cuda")
         if kappa == 1e4 and not args.no_cpu:
             vs_oracle = _orth_vs_oracle(rbo, torch, V0, c, s, s_hat)
+            oracle_time = _orth_oracle_timing(torch, V0, c, s, s_hat)
         for scheme in ("two", "one", "two_pip"):
             R64 = None
             for prec in ((rbo.PREC_FP64,) if scheme == "two_pip" else
@@ -597,7 +626,8 @@ def run_orth(rbo, torch, args):
     del V0, W, Q64
     torch.cuda.empty_cache()
     return {"n": n, "cols": c, "s": s, "s_hat": s_hat, "d": 4 * c, "results": out,
-            "sketch_types": types, "vs_oracle_20000_rows": vs_oracle}
+            "sketch_types": types, "vs_oracle_20000_rows": vs_oracle,
+            "cpu_oracle_kappa_1e4": oracle_time}
 
 
 def run_learned(rbo, torch, args):
